@@ -1,0 +1,185 @@
+"""Pins of the oracle's transforms against closed forms (Sections 1, 2 and 7).
+
+The log-polar oracle (Algorithms 1 and 2) and the direct oracle are each
+checked against analytic Radon transforms and back-projections; a few
+deliberately planted mistakes in the oracle must make those pins fail.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import bspline, direct, geometry, kernels, logpolar
+from workloads import ellipse_image, gaussian_image, random_ellipses
+
+BLOBS = [(0.2, -0.1, 0.12, 1.0), (-0.3, 0.25, 0.08, -0.7), (0.05, 0.5, 0.1, 0.4)]
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _analytic_gauss_sino(geo, blobs=BLOBS):
+    th = np.arange(geo.n_angles) * geo.dtheta
+    s = (np.arange(geo.n_det) - geo.n_det / 2) * geo.ds
+    ref = direct.gaussian_radon(th[:, None], s[None, :], blobs)
+    ref[:, ~geometry.live_bins(geo.n_det)] = 0.0
+    return ref
+
+
+def _gauss_bp_image(geo, blobs=BLOBS):
+    N = geo.N
+    x = (np.arange(N) - N / 2) * (2.0 / N)
+    out = np.zeros((N, N))
+    for cx, cy, sg, w in blobs:
+        r = np.hypot(x[None, :] - cx, x[:, None] - cy)
+        out += w * math.sqrt(2 * math.pi) * sg * direct.gaussian_bp(r, sg)
+    return np.where(geometry.disc_mask(N), out, 0.0)
+
+
+# ---------------------------------------------------------------- direct oracle
+
+def test_direct_radon_of_one_basis_function():
+    """Image samples B(i - l) B(j - k) have Q-coefficients delta_{lk}; at theta = 0 the
+    line integral is (2/N) B(col - k) (the t-integral of B is 1 pixel = 2/N), at general
+    theta it equals a brute-force Riemann sum of the closed-form basis function."""
+    N = 32
+    geo = geometry.make_geometry(N, 16, 40, 3)
+    l, k = 15, 18
+    i = np.arange(N)
+    f = bspline.B(i[:, None] - l) * bspline.B(i[None, :] - k)
+    R = direct.radon_direct(f, geo)
+    s = (np.arange(geo.n_det) - geo.n_det / 2) * geo.ds
+    live = geometry.live_bins(geo.n_det)
+    expect0 = np.where(live, (2.0 / N) * bspline.B(s * N / 2 + N / 2 - k), 0.0)
+    assert np.max(np.abs(R[0] - expect0)) < 1e-14
+    a = 5
+    th = a * geo.dtheta
+    t = np.linspace(-1.5, 1.5, 600001)
+    dt = t[1] - t[0]
+    for kk in (10, 20, 25):
+        x1 = s[kk] * math.cos(th) - t * math.sin(th)
+        x2 = s[kk] * math.sin(th) + t * math.cos(th)
+        ref = np.sum(bspline.B(x2 * N / 2 + N / 2 - l) * bspline.B(x1 * N / 2 + N / 2 - k)) * dt
+        assert R[a, kk] == pytest.approx(ref, abs=1e-9)
+
+
+def test_direct_radon_converges_to_analytic_gaussian():
+    errs = []
+    for N in (32, 64):
+        geo = geometry.make_geometry(N, 24, 3 * N // 2, 3)
+        f = gaussian_image(N, BLOBS)
+        errs.append(_rel(direct.radon_direct(f, geo), _analytic_gauss_sino(geo)))
+    assert errs[1] < 5e-5
+    assert math.log2(errs[0] / errs[1]) > 3.5  # O(h^4)
+
+
+def test_direct_radon_ellipses_close_to_analytic():
+    N = 64
+    geo = geometry.make_geometry(N, 32, 96, 3)
+    ell = random_ellipses(10, 1)
+    th = np.arange(geo.n_angles) * geo.dtheta
+    s = (np.arange(geo.n_det) - geo.n_det / 2) * geo.ds
+    ref = direct.ellipse_radon(th[:, None], s[None, :], ell)
+    assert _rel(direct.radon_direct(ellipse_image(N, ell), geo), ref) < 0.1
+
+
+def test_direct_backprojection_of_s_gaussian():
+    errs = []
+    for N in (32, 64):
+        geo = geometry.make_geometry(N, N, 3 * N // 2, 3)
+        g = _analytic_gauss_sino(geo)
+        errs.append(_rel(direct.backproject_direct(g, geo), _gauss_bp_image(geo)))
+    assert errs[1] < 1e-4
+    assert errs[0] > errs[1]
+
+
+# ---------------------------------------------------------------- log-polar oracle
+
+@pytest.mark.parametrize("M", [3, 4])
+def test_logpolar_forward_converges_to_analytic_gaussian(M):
+    errs = []
+    for N in (64, 128):
+        geo = geometry.make_geometry(N, N, 3 * N // 2, M)
+        errs.append(_rel(logpolar.forward(gaussian_image(N, BLOBS), geo), _analytic_gauss_sino(geo)))
+    assert errs[1] < 3e-5
+    assert math.log2(errs[0] / errs[1]) > 3.0
+
+
+def test_logpolar_forward_linear_interpolation_second_order():
+    errs = []
+    for N in (64, 128):
+        geo = geometry.make_geometry(N, N, 3 * N // 2, 3, interp=1)
+        errs.append(_rel(logpolar.forward(gaussian_image(N, BLOBS), geo), _analytic_gauss_sino(geo)))
+    assert errs[1] < 2e-2
+    assert math.log2(errs[0] / errs[1]) > 1.5
+
+
+@pytest.mark.parametrize("M", [3, 5])
+def test_logpolar_backprojection_of_gaussian_sinogram(M):
+    """R# of the analytic sinogram of Gaussians equals sum_k w sqrt(2 pi) s pi e^{-u} I_0(u)."""
+    errs = []
+    for N in (64, 128):
+        geo = geometry.make_geometry(N, N, 3 * N // 2, M)
+        errs.append(_rel(logpolar.backproject(_analytic_gauss_sino(geo), geo), _gauss_bp_image(geo)))
+    assert errs[1] < 2e-5
+    assert math.log2(errs[0] / errs[1]) > 3.0
+
+
+def test_logpolar_forward_conserves_mass_and_centre_per_angle():
+    """Fourier slice theorem at sigma = 0 and its first moment: int R f ds = int f and
+    int s R f ds = theta . int x f, for every angle."""
+    N = 128
+    geo = geometry.make_geometry(N, N, 3 * N // 2, 3)
+    f = gaussian_image(N, BLOBS)
+    Rf = logpolar.forward(f, geo)
+    s = (np.arange(geo.n_det) - geo.n_det / 2) * geo.ds
+    mass = sum(w * 2 * math.pi * sg * sg for _, _, sg, w in BLOBS)
+    mx = sum(w * 2 * math.pi * sg * sg * cx for cx, _, sg, w in BLOBS)
+    my = sum(w * 2 * math.pi * sg * sg * cy for _, cy, sg, w in BLOBS)
+    th = np.arange(geo.n_angles) * geo.dtheta
+    assert np.max(np.abs(Rf.sum(axis=1) * geo.ds - mass)) < 2e-5
+    assert np.max(np.abs((Rf * s).sum(axis=1) * geo.ds - (mx * np.cos(th) + my * np.sin(th)))) < 2e-5
+
+
+def test_logpolar_agrees_with_direct_oracle_on_ellipse_phantom():
+    """Config-1-style phantom at reduced size (the direct oracle is slow)."""
+    N = 64
+    geo = geometry.make_geometry(N, N, 96, 3)
+    f = ellipse_image(N, random_ellipses(10, 1))
+    sub = np.arange(0, geo.n_angles, 4)
+    Rlp = logpolar.forward(f, geo)[sub]
+    Rd = direct.radon_direct(f, geo, angle_idx=sub)
+    assert _rel(Rlp, Rd) < 0.05
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def _forward_err(geo, monkeypatch=None):
+    return _rel(logpolar.forward(gaussian_image(geo.N, BLOBS), geo), _analytic_gauss_sino(geo))
+
+
+@pytest.mark.parametrize("mistake", ["conj_kernel", "no_bhat", "no_box_comp", "no_inv_aR", "kr_shift"])
+def test_planted_mistakes_fail_the_forward_pin(monkeypatch, mistake):
+    N = 128
+    geo = geometry.make_geometry(N, N, 3 * N // 2, 3)
+    base = _forward_err(geo)
+    if mistake == "conj_kernel":
+        orig = kernels.kernel_quadrant
+        monkeypatch.setattr(kernels, "kernel_quadrant", lambda g, w, **kw: np.conj(orig(g, w, **kw)))
+    elif mistake == "no_bhat":
+        monkeypatch.setattr(kernels, "bhat2d", lambda a, b: np.ones((a, b)))
+    elif mistake == "no_box_comp":
+        monkeypatch.setattr(kernels, "box_response", lambda n, r: np.ones(n))
+    elif mistake == "no_inv_aR":
+        import dataclasses
+        geo2 = dataclasses.replace(geo)
+        orig_fwd = logpolar.forward
+        monkeypatch.setattr(logpolar, "forward", lambda f, g, **kw: orig_fwd(f, g, **kw) * g.a_R)
+        geo = geo2
+    elif mistake == "kr_shift":
+        orig = kernels.full_grid
+        monkeypatch.setattr(kernels, "full_grid", lambda q, a, b: np.roll(orig(q, a, b), 1, axis=1))
+    bad = _forward_err(geo)
+    assert bad > 20 * base

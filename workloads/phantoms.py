@@ -1,0 +1,113 @@
+"""Seeded phantoms and sinograms.
+
+Recipe (stated once, used by every test and by the benchmark):
+
+* Ellipse phantom: ``n`` ellipses, semi-axes a, b ~ U(0.05, 0.4), orientation
+  psi ~ U(0, pi), density ~ U(-1, 1); the centre is drawn uniformly in the unit
+  disc and redrawn until |c| + max(a, b) <= 0.95, so the phantom vanishes
+  outside radius 0.95.  The paper's test object is a linear combination of
+  ellipse indicators inscribed in the unit circle (Section 7); these random
+  ellipses stand in for the modified Shepp-Logan table, which is not used.
+* Pixel value: the mean of the summed indicator functions over a 4 x 4 grid of
+  sub-pixel points (area-coverage estimate).
+* Random sinogram: i.i.d. N(0, 1) entries.
+* All draws use ``numpy.random.default_rng(seed)`` (PCG64).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Ellipse:
+    cx: float
+    cy: float
+    a: float
+    b: float
+    psi: float
+    density: float
+
+
+def random_ellipses(n: int, seed: int, max_radius: float = 0.95) -> list[Ellipse]:
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        a, b = rng.uniform(0.05, 0.4, size=2)
+        psi = rng.uniform(0.0, np.pi)
+        dens = rng.uniform(-1.0, 1.0)
+        reach = max(a, b)
+        while True:
+            cx, cy = rng.uniform(-1.0, 1.0, size=2)
+            if np.hypot(cx, cy) + reach <= max_radius:
+                break
+        out.append(Ellipse(float(cx), float(cy), float(a), float(b), float(psi), float(dens)))
+    return out
+
+
+def _grid(N: int, sub: int):
+    h = 2.0 / N
+    base = (np.arange(N) - N / 2) * h
+    off = ((np.arange(sub) + 0.5) / sub - 0.5) * h
+    return base, off
+
+
+def ellipse_image(N: int, ellipses: list[Ellipse], sub: int = 4) -> np.ndarray:
+    """Area-coverage rasterisation of a sum of ellipse indicators, float64 [N, N]."""
+    base, off = _grid(N, sub)
+    img = np.zeros((N, N))
+    for e in ellipses:
+        c, s = np.cos(e.psi), np.sin(e.psi)
+        reach = max(e.a, e.b) + 2.0 / N
+        rows = np.nonzero(np.abs(base - e.cy) <= reach)[0]
+        cols = np.nonzero(np.abs(base - e.cx) <= reach)[0]
+        if rows.size == 0 or cols.size == 0:
+            continue
+        acc = np.zeros((rows.size, cols.size))
+        for oy in off:
+            y = (base[rows] + oy - e.cy)[:, None]
+            for ox in off:
+                x = (base[cols] + ox - e.cx)[None, :]
+                u = x * c + y * s
+                v = -x * s + y * c
+                acc += ((u / e.a) ** 2 + (v / e.b) ** 2 <= 1.0)
+        img[np.ix_(rows, cols)] += e.density * acc / (sub * sub)
+    return img
+
+
+def gaussian_image(N: int, blobs) -> np.ndarray:
+    """Point samples of sum_k w_k exp(-|x - c_k|^2 / (2 s_k^2)); blobs = [(cx, cy, s, w), ...]."""
+    h = 2.0 / N
+    x = (np.arange(N) - N / 2) * h
+    X1, X2 = np.meshgrid(x, x)
+    img = np.zeros((N, N))
+    for cx, cy, s, w in blobs:
+        img += w * np.exp(-((X1 - cx) ** 2 + (X2 - cy) ** 2) / (2.0 * s * s))
+    return img
+
+
+def smooth_random_image(N: int, seed: int, n_blobs: int = 24) -> np.ndarray:
+    """A seeded sum of Gaussian bumps (widths 0.03-0.2) inside radius 0.8."""
+    rng = np.random.default_rng(seed)
+    blobs = []
+    for _ in range(n_blobs):
+        s = rng.uniform(0.03, 0.2)
+        while True:
+            cx, cy = rng.uniform(-0.8, 0.8, size=2)
+            if np.hypot(cx, cy) <= 0.8 - s:
+                break
+        blobs.append((cx, cy, s, rng.uniform(-1.0, 1.0)))
+    return gaussian_image(N, blobs)
+
+
+def random_sinogram(n_angles: int, n_det: int, seed: int) -> np.ndarray:
+    """i.i.d. N(0, 1) sinogram, float64 [n_angles, n_det]."""
+    return np.random.default_rng(seed).standard_normal((n_angles, n_det))
+
+
+def slice_sizes(count: int, seed: int, choices=(256, 512, 1024, 2048, 4096)) -> list[int]:
+    """Uneven slice sizes N drawn uniformly from ``choices``."""
+    rng = np.random.default_rng(seed)
+    return [int(v) for v in rng.choice(np.asarray(choices), size=count)]
