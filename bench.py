@@ -1,0 +1,390 @@
+"""Benchmark: log-polar Radon transform R + back-projection R# at N = 2048 on GB300.
+
+One step = one forward transform R (image -> sinogram) plus one back-projection R#
+(sinogram -> image) of the 2048 x 2048 / 2048-angle / 3072-bin workload, cubic B-splines,
+M = 3 partitions, FP32, inputs resident in HBM.  The L2 cache is flushed (a 256 MB write)
+before every timed step, outside the timed interval.  Under torchrun every rank runs the same
+per-GPU work on its own slices (weak scaling, no collective in the data path).
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this build) on the host
+cores, on a bounded sample of the same workload.
+
+Prints one JSON line (rank 0).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Radon+back-projection samples/sec and % HBM roofline at N=2048, err vs FP64 oracle"
+UNIT = "samples/s"
+N, N_ANGLES, N_DET, INTERP, M = 2048, 2048, 3072, 3, 3
+WORKLOAD = "radon_pair_N2048_A2048_D3072_cubic_M3"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _config():
+    return {
+        "workload": WORKLOAD,
+        "N": N, "n_angles": N_ANGLES, "n_det": N_DET, "interp_order": INTERP, "n_partitions": M,
+        "step": "one R (image->sinogram) + one R# (sinogram->image)",
+        "phantom": "50 random ellipses, seed 2; sinogram i.i.d. N(0,1), seed 3",
+        "l2": "flushed before each timed step (256 MB write, outside the timed interval)",
+    }
+
+
+def _samples_per_step():
+    return N_ANGLES * N_DET + N * N
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- roofline model
+
+def stage_bytes(info):
+    """Algorithmic DRAM bytes per launch of each stage (unique bytes a stage must move)."""
+    n, na, nd, mm = info["N"], info["n_angles"], info["n_det"], info["n_partitions"]
+    nh, nr = info["n_theta_half"], info["N_rho"]
+    nc1 = nr // 2 + 1
+    spec_in = mm * nh * nc1 * 8          # half spectrum of the sampled rows
+    spec_out = mm * (nh + 4) * nc1 * 8   # kept rows after the theta convolution
+    ylp = mm * (nh + 4) * nr * 4         # log-polar coefficients
+    kern = (info["n_theta"] // 2 + 1) * nc1 * 8
+    img = 4 * n * n
+    sino = 4 * na * nd
+    disc = 4 * math.pi / 4 * n * n       # coefficient pixels inside the disc (read once per launch)
+    return {
+        "prefilter_image": 2 * img,
+        "rows_fwd": disc + spec_in,
+        "columns_fwd": spec_in + kern + spec_out,
+        "rows_inv_fwd": spec_out + ylp,
+        "gather_sino": ylp + sino,
+        "prefilter_sino": 2 * sino,
+        "rows_bp": sino + spec_in,
+        "columns_bp": spec_in + kern + spec_out,
+        "rows_inv_bp": spec_out + ylp,
+        "gather_image": ylp + img,
+    }
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1506_00014_gb300 as rl
+    from paper_1506_00014_gb300 import build as _build
+    from workloads import ellipse_image, random_ellipses, random_sinogram
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if _build.needs_build() and rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+
+    plan = rl.radon_plan_create(N, N_ANGLES, N_DET, INTERP, M)
+    info = plan.info
+    f = ellipse_image(N, random_ellipses(50, 2 + 1000 * rank)).astype(np.float32)
+    g = random_sinogram(N_ANGLES, N_DET, 3 + 1000 * rank).astype(np.float32)
+    f_d = torch.from_numpy(f).to(dev)
+    g_d = torch.from_numpy(g).to(dev)
+    sino_d = torch.empty((N_ANGLES, N_DET), dtype=torch.float32, device=dev)
+    img_d = torch.empty((N, N), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        rl.radon_forward(plan, f_d, sino_d, stream)
+        rl.radon_backproject(plan, g_d, img_d, stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: per-step CUDA events around the transforms only; the L2 flush sits between
+    rl.radon_profile_enable(plan, True)
+    rl.radon_profile_read(plan)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    stage = rl.radon_profile_read(plan)
+    rl.radon_profile_enable(plan, False)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * _samples_per_step() * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant stage
+    nbytes = stage_bytes(info)
+    dom = max(stage, key=lambda k: stage[k][0])
+    dom_ms = stage[dom][0] / max(1, stage[dom][1])
+    peak, peak_kind = _peaks()
+    achieved = nbytes[dom] / (dom_ms / 1e3) / 1e9
+    stage_ms = {k: round(v[0] / max(1, v[1]), 4) for k, v in stage.items()}
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as fh:
+                traffic = json.load(fh).get(dom)
+        except (OSError, ValueError):
+            traffic = None
+
+    # end to end through the host-buffer C ABI entry points (pinned host memory)
+    h_f = torch.from_numpy(f).pin_memory()
+    h_g = torch.from_numpy(g).pin_memory()
+    h_s = torch.empty((N_ANGLES, N_DET), dtype=torch.float32).pin_memory()
+    h_i = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        rl.radon_forward_host(plan, h_f, h_s, stream)
+        rl.radon_backproject_host(plan, h_g, h_i, stream)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rl.radon_forward_host(plan, h_f, h_s, stream)
+        rl.radon_backproject_host(plan, h_g, h_i, stream)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {
+        "value": world * _samples_per_step() * args.steps / e2e_s,
+        "unit": UNIT,
+        "h2d_bytes_per_step": 4 * (N * N + N_ANGLES * N_DET),
+        "d2h_bytes_per_step": 4 * (N_ANGLES * N_DET + N * N),
+    }
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(f, g)
+
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(),
+        "roofline": {
+            "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "algorithmic_bytes": nbytes[dom], "ms_per_launch": dom_ms,
+        },
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 10 * args.steps,
+        "clocks": clk,
+        "stage_ms_per_launch": stage_ms,
+        "pixel_angle_updates_per_s": world * N * N * N_ANGLES * args.steps / (total_ms / 1e3),
+    }
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(f, g, partitions=(0,)):
+    """FP64 oracle on the host cores: R and R# of the same inputs restricted to partition 0 (of 3);
+    kernel tables and DFT matrices are set up outside the timed interval."""
+    import numpy as np
+
+    from oracle import geometry, kernels, logpolar
+
+    geo = geometry.make_geometry(N, N_ANGLES, N_DET, M, INTERP)
+    KR = kernels.multiplier(geo, "R")
+    KB = kernels.multiplier(geo, "B")
+    dft = logpolar._Dft(geo)
+    t0 = time.perf_counter()
+    logpolar.forward(f.astype(np.float64), geo, K=KR, dft=dft, partitions=partitions)
+    logpolar.backproject(g.astype(np.float64), geo, K=KB, dft=dft, partitions=partitions)
+    dt = time.perf_counter() - t0
+    frac = len(partitions) / M
+    return {
+        "value": frac * _samples_per_step() / dt,
+        "unit": UNIT,
+        "cores": os.cpu_count(),
+        "kind": "oracle",
+        "sample": f"R and R# of the N=2048 workload restricted to partition(s) {list(partitions)} of {M} "
+                  f"({dt:.1f} s); value scaled by that fraction",
+    }
+
+
+def run_reference(args):
+    import numpy as np
+
+    from workloads import ellipse_image, random_ellipses, random_sinogram
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    f = ellipse_image(N, random_ellipses(50, 2)).astype(np.float32)
+    g = random_sinogram(N_ANGLES, N_DET, 3).astype(np.float32)
+    vals = []
+    last = None
+    t_start = time.perf_counter()
+    for _ in range(args.steps):  # bounded: stop after ~2 minutes of oracle time
+        last = cpu_baseline(f, g)
+        vals.append(last["value"])
+        if time.perf_counter() - t_start > 120.0:
+            break
+    value = statistics.median(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": len(vals), "warmup": 0, "ms_per_step": 1e3 * _samples_per_step() / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": last["sample"] if last else ""},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_once():
+    import numpy as np
+    import torch
+
+    import paper_1506_00014_gb300 as rl
+    from workloads import ellipse_image, random_ellipses, random_sinogram
+
+    plan = rl.radon_plan_create(N, N_ANGLES, N_DET, INTERP, M)
+    f = torch.from_numpy(ellipse_image(N, random_ellipses(50, 2)).astype(np.float32)).cuda()
+    g = torch.from_numpy(random_sinogram(N_ANGLES, N_DET, 3).astype(np.float32)).cuda()
+    s = torch.empty((N_ANGLES, N_DET), dtype=torch.float32, device="cuda")
+    i = torch.empty((N, N), dtype=torch.float32, device="cuda")
+    rl.radon_forward(plan, f, s)
+    rl.radon_backproject(plan, g, i)
+    torch.cuda.synchronize()
+    print(json.dumps({"once": WORKLOAD, "sino_sum": float(s.double().sum()), "img_sum": float(i.double().sum())}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--once", action="store_true",
+                    help="one untimed R + R# on the workload (for profiler captures); prints a short line")
+    args = ap.parse_args()
+    if args.once:
+        run_once()
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

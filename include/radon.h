@@ -1,0 +1,131 @@
+/*
+ * radon.h -- C ABI of the log-polar Radon transform / back-projection library (libradon.so).
+ *
+ * The library evaluates the Radon transform R and its adjoint, the back-projection R#, of
+ * Andersson, Carlsson and Nikitin, "Fast algorithms and efficient GPU implementations for the
+ * Radon transform and the back-projection operator represented as convolution operators"
+ * (arXiv 1506.00014), as convolutions in log-polar coordinates:
+ *   R : Algorithm 1 (Section 6) -- pre-filter Q (Eq. Qfrecursive), resampling of T_m f onto the
+ *       log-polar grid (Eq. Tdef, Eq. Lopolargrid_f, Eq. Lopolargrid_polar), FFT convolution with
+ *       zeta / B-hat (Eq. exprcoef1, Eq. Bhat), resampling at S_m (Eq. Radon_all_pb, Eq. Sm_def).
+ *   R#: Algorithm 2 (Section 6) -- the mirrored chain with zeta# (Eq. exprcoef2,
+ *       Eq. backproj_lpp) and a sum over the M partitions.
+ *
+ * Conventions (all arrays are dense, row-major, FP32, in the caller's memory):
+ *   image    f[i][j], i, j in [0, N): pixel centre x1 = (j - N/2) * 2/N, x2 = (i - N/2) * 2/N;
+ *            the object is taken to vanish outside the open unit disc, so input pixels with
+ *            |x| >= 1 are ignored and output pixels with |x| >= 1 are written as 0.
+ *   sinogram g[a][k], a in [0, n_angles), k in [0, n_det): theta_a = a * pi / n_angles,
+ *            s_k = (k - n_det/2) * ds, ds = 2 sqrt(2) / n_det; bins with |s_k| >= 1 are written
+ *            as 0 by R and ignored by R#.
+ *   R f(theta, s) = int f(x) delta(x . theta - s) dx               (Eq. radon_def)
+ *   R# g(x)       = int_0^pi g(theta, x . theta) dtheta            (adjoint of R on [0, pi) x R)
+ *
+ * Calls are asynchronous and ordered on the CUDA stream passed as `stream` (a cudaStream_t,
+ * NULL = legacy default stream).  Device pointers must come from cudaMalloc (or a caching
+ * allocator over it) on the current device.  A plan owns its tables and its scratch memory:
+ * it must not be used by two calls that can overlap on the GPU (one stream at a time).
+ *
+ * Every entry point returns a radon_status.  No call throws, exits or falls back to the CPU.
+ */
+#ifndef RADON_H_
+#define RADON_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RADON_OK = 0,
+  RADON_INVALID_ARG = 1,     /* bad size, NULL pointer, unknown option */
+  RADON_OUT_OF_MEMORY = 2,   /* a device or host allocation failed */
+  RADON_CUDA_ERROR = 3,      /* a CUDA runtime call or kernel launch failed */
+  RADON_TIMEOUT = 4,         /* a bounded device-side wait gave up */
+  RADON_NOT_SUPPORTED = 5    /* valid request outside what this build handles */
+} radon_status;
+
+typedef enum {
+  RADON_FILTER_RAMP = 0,         /* |sigma|                                   (Eq. ramp)   */
+  RADON_FILTER_SHEPP_LOGAN = 1,  /* |sigma| sinc(sigma / (2 sigma_max))       (Eq. SLfilt) */
+  RADON_FILTER_COSINE = 2        /* |sigma| cos(pi sigma / (2 sigma_max))     (Eq. cosfilt)*/
+} radon_filter;
+
+typedef struct radon_plan_s* radon_plan;
+
+/* Derived discretisation (Sections 2 and 4); what the plan computes, for tests and oracles. */
+typedef struct {
+  int N, n_angles, n_det, interp_order, n_partitions;
+  int N_rho;          /* rho samples: Eq. vrho bound rounded up to an even 7-smooth integer   */
+  int n_theta_half;   /* angular samples per partition (centre half of the FFT grid)          */
+  int n_theta;        /* angular FFT length, 2 * n_theta_half, period [-beta, beta)           */
+  int r;              /* fine angular sub-samples per coarse angle (Omega_lp -> Omega_p)       */
+  int n_quad;         /* trapezoid nodes used for the kernel integrals (Eq. weightsa)          */
+  double beta, a_R, a_r, L;       /* pi/M, Eq. aconst, L = -log(a_r)                           */
+  double d_phi, d_rho, d_s, d_theta;
+  size_t device_bytes;            /* device memory owned by the plan (tables + scratch)        */
+} radon_plan_info;
+
+/* Create a plan.  N even and >= 8; n_angles >= 2; n_det >= 4; interp_order 1 (linear) or 3
+ * (cubic B-spline); n_partitions M >= 3.  Computes the geometry and the kernel transforms
+ * zeta_hat / B_hat, zeta#_hat / B_hat in FP64 on the host (trapezoid rule with the end
+ * corrections of Eq. weightsa), uploads them as FP32 and allocates the scratch buffers on the
+ * current device.  Synchronous.  *out is set to NULL on failure. */
+int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int interp_order,
+                      int n_partitions);
+
+/* Release a plan (NULL is ignored).  Synchronises the device first. */
+void radon_plan_destroy(radon_plan plan);
+
+/* Fill *out with the plan's derived sizes. */
+int radon_plan_get_info(radon_plan plan, radon_plan_info* out);
+
+/* R: d_image [N][N] -> d_sino [n_angles][n_det] (overwritten).  Algorithm 1. */
+int radon_forward(radon_plan plan, const float* d_image, float* d_sino, void* stream);
+
+/* R#: d_sino [n_angles][n_det] -> d_image [N][N] (overwritten).  Algorithm 2. */
+int radon_backproject(radon_plan plan, const float* d_sino, float* d_image, void* stream);
+
+/* Filtered back-projection f = R# W g (Eq. FBP): W filters each sinogram row along s with the
+ * transfer function selected by `filter` (band-limited to |sigma| <= sigma_max = 1/(2 ds)),
+ * then R# is applied.  d_sino is not modified. */
+int radon_fbp(radon_plan plan, const float* d_sino, float* d_image, int filter, void* stream);
+
+/* Same as radon_forward / radon_backproject but with HOST buffers: the call copies the input to
+ * plan-owned device memory, runs the transform on `stream` and copies the result back; it
+ * returns after the result is in host memory.  Page-locked buffers give the fastest copies. */
+int radon_forward_host(radon_plan plan, const float* h_image, float* h_sino, void* stream);
+int radon_backproject_host(radon_plan plan, const float* h_sino, float* h_image, void* stream);
+
+/* Host-only helpers (no GPU needed).
+ * radon_geometry: the derived sizes a plan with these arguments would use (device_bytes = 0).
+ * radon_kernel_quadrant: the FP64 kernel coefficients zeta_hat (which = 0) or zeta#_hat
+ *   (which = 1) for k_theta in [0, n_theta/2] (slow index) and k_rho in [0, N_rho/2] (fast
+ *   index), as interleaved (re, im) pairs; `out` holds 2 * (n_theta/2+1) * (N_rho/2+1) doubles.
+ *   These are the raw integrals of Eq. exprcoef1 / exprcoef2, before any division. */
+int radon_geometry(int N, int n_angles, int n_det, int interp_order, int n_partitions,
+                   radon_plan_info* out);
+int radon_kernel_quadrant(int N, int n_angles, int n_det, int n_partitions, int which,
+                          double* out);
+
+/* Per-stage timing (profiling aid).  While enabled, every transform records a CUDA event on its
+ * stream after each of its kernel launches.  radon_profile_read waits for the recorded events,
+ * adds each stage's elapsed milliseconds to ms[stage] and its launch count to launches[stage]
+ * (arrays of RADON_NUM_STAGES entries, not cleared by the call), then forgets the events.
+ * Stages: 0 image pre-filter, 1 forward row sampling + rho FFT, 2 forward theta convolution,
+ * 3 forward inverse rho FFT, 4 sinogram gather, 5 sinogram pre-filter, 6 back-projection row
+ * sampling + rho FFT, 7 back-projection theta convolution, 8 back-projection inverse rho FFT,
+ * 9 image gather. */
+#define RADON_NUM_STAGES 10
+int radon_profile_enable(radon_plan plan, int enable);
+int radon_profile_read(radon_plan plan, double* ms, int* launches);
+
+/* Human-readable name of a status code (static string). */
+const char* radon_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RADON_H_ */

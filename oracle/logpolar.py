@@ -62,7 +62,7 @@ def logpolar_convolution(h_central: np.ndarray, K: np.ndarray, geo, dft: _Dft | 
     dft = dft or _Dft(geo)
     nh, nt, nr = geo.n_th_h, geo.n_theta, geo.N_rho
     rows_in = np.arange(nh // 2, nh // 2 + nh)
-    rows_out = np.arange(nh // 2 - HALO_LO, nh // 2 + nh + HALO_HI)
+    rows_out = np.arange(nh // 2 - HALO_LO, nh // 2 + nh + HALO_HI) % nt  # output is nt-periodic
     A = h_central @ dft.Frho                  # DFT along rho (F is symmetric)
     H = dft.Fth[:, rows_in] @ A               # DFT along theta of the zero-padded columns
     H = H * K
@@ -106,7 +106,7 @@ def forward(f: np.ndarray, geo, K: np.ndarray | None = None, dft: _Dft | None = 
     """
     N, M, r = geo.N, geo.M, geo.r
     nh, nr = geo.n_th_h, geo.N_rho
-    c = image_coefficients(f, geo)                     # step 1: Q f
+    c = image_coefficients(f, geo)                     # pre-filter Q
     K = kernels.multiplier(geo, "R") if K is None else K
     dft = dft or _Dft(geo)
     rho = geo.rho(np.arange(nr))
@@ -129,10 +129,10 @@ def forward(f: np.ndarray, geo, K: np.ndarray | None = None, dft: _Dft | None = 
             x2 = sm * u1 + cm * u2
             col = x1 * (N / 2) + N / 2
             row = x2 * (N / 2) + N / 2
-            vals = bspline.interp2d(c, row, col, order=geo.interp)         # step 3: resample
-            h[jj - 0, :] = vals.mean(axis=1) * erho[None, :]               # steps 4-5
-        y = logpolar_convolution(h, K, geo, dft)                           # step 6
-        # step 7: resample from S_m^{-1} Omega_p to Sigma
+            vals = bspline.interp2d(c, row, col, order=geo.interp)         # resample T_m f on Omega_lp
+            h[jj - 0, :] = vals.mean(axis=1) * erho[None, :]               # downsample to Omega_p, times e^rho
+        y = logpolar_convolution(h, K, geo, dft)                           # convolution with zeta / B-hat
+        # resample from S_m^{-1} Omega_p to Sigma
         for a in range(geo.n_angles):
             am, num, flip = angle_partition(a, geo.n_angles, M)
             if am != m:
@@ -152,7 +152,7 @@ def backproject(g: np.ndarray, geo, K: np.ndarray | None = None, dft: _Dft | Non
     """Algorithm 2.  Returns R# g on X, float64 [N, N]."""
     N, M = geo.N, geo.M
     nh, nr = geo.n_th_h, geo.N_rho
-    E = sinogram_coefficients(g, geo)                  # step 1: Q g
+    E = sinogram_coefficients(g, geo)                  # pre-filter Q
     K = kernels.multiplier(geo, "B") if K is None else K
     dft = dft or _Dft(geo)
     erho = np.exp(geo.rho(np.arange(nr)))
@@ -171,13 +171,13 @@ def backproject(g: np.ndarray, geo, K: np.ndarray | None = None, dft: _Dft | Non
             cth = np.broadcast_to(theta / geo.dtheta, s.shape)
             cs = s / geo.ds + geo.n_det / 2
             G[jj, :] = bspline.interp2d(E, cth, cs, order=geo.interp,
-                                        mode0="periodic", mode1="zero")       # step 3
-        y = logpolar_convolution(G, K, geo, dft)                               # step 4
+                                        mode0="periodic", mode1="zero")       # resample g(S_m)
+        y = logpolar_convolution(G, K, geo, dft)                               # convolution with zeta# / B-hat
         cm, sm = math.cos(m * geo.beta), math.sin(m * geo.beta)
         y1 = geo.a_R * (cm * x1 + sm * x2) + 1.0 - geo.a_R                     # T_m x
         y2 = geo.a_R * (-sm * x1 + cm * x2)
         cth = np.arctan2(y2, y1) / geo.dphi + nh // 2 + HALO_LO
         crho = 0.5 * np.log(y1 * y1 + y2 * y2) / geo.drho + nr - 1
         img[ii, jj_pix] += bspline.interp2d(y, cth, crho, order=geo.interp,
-                                            mode0="zero", mode1="periodic")    # steps 5-7
+                                            mode0="zero", mode1="periodic")    # to X, summed over m
     return img

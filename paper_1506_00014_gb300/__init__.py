@@ -1,0 +1,27 @@
+"""GB300-native log-polar Radon transform and back-projection (arXiv 1506.00014).
+
+The transforms run in hand-written CUDA kernels for sm_103a inside ``libradon.so``
+(C ABI in ``include/radon.h``); ``binding`` marshals arguments to it.
+"""
+
+from .binding import (  # noqa: F401
+    RADON_FILTER_COSINE,
+    RADON_FILTER_RAMP,
+    RADON_FILTER_SHEPP_LOGAN,
+    RadonError,
+    RadonPlan,
+    load,
+    radon_backproject,
+    radon_backproject_host,
+    radon_fbp,
+    radon_forward,
+    radon_forward_host,
+    radon_geometry,
+    radon_kernel_quadrant,
+    radon_plan_create,
+    radon_plan_destroy,
+    radon_plan_get_info,
+    radon_profile_enable,
+    radon_profile_read,
+    radon_status_string,
+)

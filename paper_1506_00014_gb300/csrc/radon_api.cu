@@ -1,0 +1,345 @@
+// C ABI of libradon (declared in include/radon.h): plan lifecycle and transform entry points.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "plan_host.h"
+#include "radon.h"
+#include "radon_kernels.cuh"
+
+struct radon_plan_s {
+  radon_plan_info info;
+  radon::DevPlan dp;
+  int device = -1;
+  void* table_mem = nullptr;
+  void* scratch_mem = nullptr;
+  float* io_image = nullptr;  // device staging for the host-buffer entry points
+  float* io_sino = nullptr;
+  // per-stage event timing (radon_profile_enable / radon_profile_read)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<int> prof_stage;  // stage id recorded with each used event (-1: start of a call)
+  size_t prof_used = 0;
+  cudaError_t prof_err = cudaSuccess;
+};
+
+namespace {
+
+int status_of(cudaError_t e) {
+  if (e == cudaSuccess) return RADON_OK;
+  if (e == cudaErrorMemoryAllocation) return RADON_OUT_OF_MEMORY;
+  return RADON_CUDA_ERROR;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Packs host vectors into one device allocation.
+class TablePacker {
+ public:
+  template <class T>
+  size_t add(const std::vector<T>& v) {
+    const size_t off = total_;
+    parts_.push_back({off, v.data(), v.size() * sizeof(T)});
+    total_ = align_up(total_ + v.size() * sizeof(T), 256);
+    return off;
+  }
+  size_t total() const { return total_; }
+  cudaError_t upload(void* dev) const {
+    for (const auto& p : parts_) {
+      if (!p.bytes) continue;
+      cudaError_t e = cudaMemcpy(static_cast<char*>(dev) + p.off, p.src, p.bytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+ private:
+  struct Part {
+    size_t off;
+    const void* src;
+    size_t bytes;
+  };
+  std::vector<Part> parts_;
+  size_t total_ = 0;
+};
+
+void copy_radices(const radon::Radices& r, radon::RadixList* out) {
+  out->n = r.n;
+  out->count = r.count;
+  for (int i = 0; i < 24; ++i) out->r[i] = i < r.count ? r.r[i] : 0;
+}
+
+void prof_mark(void* ctx, int stage, cudaStream_t st) {
+  radon_plan_s* p = static_cast<radon_plan_s*>(ctx);
+  if (p->prof_used == p->prof_pool.size()) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+      p->prof_err = e;
+      return;
+    }
+    p->prof_pool.push_back(ev);
+    p->prof_stage.push_back(0);
+  }
+  cudaError_t e = cudaEventRecord(p->prof_pool[p->prof_used], st);
+  if (e != cudaSuccess) {
+    p->prof_err = e;
+    return;
+  }
+  p->prof_stage[p->prof_used++] = stage;
+}
+
+radon::StageHook hook_of(radon_plan_s* p) {
+  radon::StageHook h;
+  h.mark = p->prof_on ? prof_mark : nullptr;
+  h.ctx = p;
+  return h;
+}
+
+bool on_plan_device(const radon_plan_s* p) {
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev == p->device;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* radon_status_string(int status) {
+  switch (status) {
+    case RADON_OK: return "ok";
+    case RADON_INVALID_ARG: return "invalid argument";
+    case RADON_OUT_OF_MEMORY: return "out of memory";
+    case RADON_CUDA_ERROR: return "CUDA error";
+    case RADON_TIMEOUT: return "timeout";
+    case RADON_NOT_SUPPORTED: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+int radon_geometry(int N, int n_angles, int n_det, int interp_order, int n_partitions, radon_plan_info* out) {
+  return radon::compute_geometry(N, n_angles, n_det, interp_order, n_partitions, out);
+}
+
+int radon_kernel_quadrant(int N, int n_angles, int n_det, int n_partitions, int which, double* out) {
+  if (!out || (which != 0 && which != 1)) return RADON_INVALID_ARG;
+  radon_plan_info g;
+  int s = radon::compute_geometry(N, n_angles, n_det, 3, n_partitions, &g);
+  if (s != RADON_OK) return s;
+  std::vector<double> v;
+  radon::kernel_quadrant(g, which, &v);
+  std::memcpy(out, v.data(), v.size() * sizeof(double));
+  return RADON_OK;
+}
+
+void radon_plan_destroy(radon_plan plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  for (cudaEvent_t ev : plan->prof_pool) cudaEventDestroy(ev);
+  cudaFree(plan->table_mem);
+  cudaFree(plan->scratch_mem);
+  delete plan;
+}
+
+int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int interp_order, int n_partitions) {
+  if (!out) return RADON_INVALID_ARG;
+  *out = nullptr;
+  radon_plan_info g;
+  int s = radon::compute_geometry(N, n_angles, n_det, interp_order, n_partitions, &g);
+  if (s != RADON_OK) return s;
+  radon::HostTables t;
+  s = radon::build_tables(g, &t);
+  if (s != RADON_OK) return s;
+
+  radon_plan_s* p = new (std::nothrow) radon_plan_s();
+  if (!p) return RADON_OUT_OF_MEMORY;
+  p->info = g;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return RADON_CUDA_ERROR;
+  }
+  radon::DevPlan& d = p->dp;
+  std::memset(&d, 0, sizeof(d));
+  d.N = N;
+  d.n_angles = n_angles;
+  d.n_det = n_det;
+  d.M = n_partitions;
+  d.interp = interp_order;
+  d.N_rho = g.N_rho;
+  d.nh = g.n_theta_half;
+  d.n_theta = g.n_theta;
+  d.r = g.r;
+  d.nc = g.N_rho / 2;
+  d.img_pitch = N + 2 * radon::kPad;
+  d.sino_pitch = static_cast<int>(align_up(n_det + 1 + 2 * radon::kPad, 4));
+  d.x_pitch = static_cast<int>(align_up(d.nc + 1, 4));
+  d.y_pitch = static_cast<int>(align_up(g.N_rho + 2 * radon::kPad, 4));
+  d.n_eanc = (g.N_rho + radon::kETile - 1) / radon::kETile;
+  d.n_ktiles = (n_det + radon::kKTile - 1) / radon::kKTile;
+  d.n_ptiles = (N + radon::kPTile - 1) / radon::kPTile;
+  d.col_group = 4;
+  while (d.col_group > 1 && 2 * static_cast<size_t>(d.col_group) * g.n_theta * sizeof(float2) > (200u << 10)) d.col_group /= 2;
+  if (2 * static_cast<size_t>(d.col_group) * g.n_theta * sizeof(float2) > (220u << 10) ||
+      2 * static_cast<size_t>(g.N_rho / 2) * sizeof(float2) > (220u << 10)) {
+    delete p;
+    return RADON_NOT_SUPPORTED;
+  }
+  d.inv_drho = static_cast<float>(1.0 / g.d_rho);
+  d.inv_dphi = static_cast<float>(1.0 / g.d_phi);
+  d.inv_aR = static_cast<float>(1.0 / g.a_R);
+  d.d_s = static_cast<float>(g.d_s);
+  copy_radices(t.rad_rho, &d.rad_rho);
+  copy_radices(t.rad_th, &d.rad_th);
+
+  TablePacker tp;
+  const size_t o_tw_rho = tp.add(t.tw_rho), o_tw_r2c = tp.add(t.tw_r2c), o_tw_th = tp.add(t.tw_th);
+  const size_t o_kf = tp.add(t.k_fwd), o_kb = tp.add(t.k_bp);
+  const size_t o_frow = tp.add(t.fwd_row), o_fm = tp.add(t.fwd_m), o_fe = tp.add(t.fwd_e), o_fea = tp.add(t.fwd_eanc);
+  const size_t o_fang = tp.add(t.fwd_ang), o_fanc = tp.add(t.fwd_anc);
+  const size_t o_bth = tp.add(t.bp_th), o_bc = tp.add(t.bp_c), o_be = tp.add(t.bp_e);
+  const size_t o_banc = tp.add(t.bp_anc), o_bm = tp.add(t.bp_m), o_fir = tp.add(t.fir);
+
+  const size_t nrow = static_cast<size_t>(d.nh) + radon::kHaloLo + radon::kHaloHi;
+  size_t sc = 0;
+  auto take = [&](size_t bytes) {
+    const size_t off = sc;
+    sc = align_up(sc + bytes, 256);
+    return off;
+  };
+  const size_t s_img = take(sizeof(float) * static_cast<size_t>(d.img_pitch) * d.img_pitch);
+  const size_t s_sino = take(sizeof(float) * static_cast<size_t>(n_angles) * d.sino_pitch);
+  const size_t s_x = take(sizeof(float2) * static_cast<size_t>(d.M) * d.nh * d.x_pitch);
+  const size_t s_ys = take(sizeof(float2) * static_cast<size_t>(d.M) * nrow * d.x_pitch);
+  const size_t s_y = take(sizeof(float) * static_cast<size_t>(d.M) * nrow * d.y_pitch);
+  const size_t s_io_img = take(sizeof(float) * static_cast<size_t>(N) * N);
+  const size_t s_io_sino = take(sizeof(float) * static_cast<size_t>(n_angles) * n_det);
+
+  cudaError_t e = cudaMalloc(&p->table_mem, tp.total());
+  if (e == cudaSuccess) e = tp.upload(p->table_mem);
+  if (e == cudaSuccess) e = cudaMalloc(&p->scratch_mem, sc);
+  if (e == cudaSuccess) e = cudaMemset(p->scratch_mem, 0, sc);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    radon_plan_destroy(p);
+    return status_of(e);
+  }
+  char* tb = static_cast<char*>(p->table_mem);
+  char* sb = static_cast<char*>(p->scratch_mem);
+  d.tw_rho = reinterpret_cast<const float2*>(tb + o_tw_rho);
+  d.tw_r2c = reinterpret_cast<const float2*>(tb + o_tw_r2c);
+  d.tw_th = reinterpret_cast<const float2*>(tb + o_tw_th);
+  d.k_fwd = reinterpret_cast<const float2*>(tb + o_kf);
+  d.k_bp = reinterpret_cast<const float2*>(tb + o_kb);
+  d.fwd_row = reinterpret_cast<const float4*>(tb + o_frow);
+  d.fwd_m = reinterpret_cast<const float4*>(tb + o_fm);
+  d.fwd_e = reinterpret_cast<const float2*>(tb + o_fe);
+  d.fwd_eanc = reinterpret_cast<const float2*>(tb + o_fea);
+  d.fwd_ang = reinterpret_cast<const int4*>(tb + o_fang);
+  d.fwd_anc = reinterpret_cast<const int4*>(tb + o_fanc);
+  d.bp_th = reinterpret_cast<const int2*>(tb + o_bth);
+  d.bp_c = reinterpret_cast<const int2*>(tb + o_bc);
+  d.bp_e = reinterpret_cast<const int2*>(tb + o_be);
+  d.bp_anc = reinterpret_cast<const int4*>(tb + o_banc);
+  d.bp_m = reinterpret_cast<const float2*>(tb + o_bm);
+  d.fir = reinterpret_cast<const float*>(tb + o_fir);
+  d.coef_img = reinterpret_cast<float*>(sb + s_img);
+  d.coef_sino = reinterpret_cast<float*>(sb + s_sino);
+  d.xspec = reinterpret_cast<float2*>(sb + s_x);
+  d.yspec = reinterpret_cast<float2*>(sb + s_ys);
+  d.ylp = reinterpret_cast<float*>(sb + s_y);
+  p->io_image = reinterpret_cast<float*>(sb + s_io_img);
+  p->io_sino = reinterpret_cast<float*>(sb + s_io_sino);
+  p->info.device_bytes = tp.total() + sc;
+
+  e = radon::configure_kernels(d);
+  if (e != cudaSuccess) {
+    radon_plan_destroy(p);
+    return status_of(e);
+  }
+  *out = p;
+  return RADON_OK;
+}
+
+int radon_plan_get_info(radon_plan plan, radon_plan_info* out) {
+  if (!plan || !out) return RADON_INVALID_ARG;
+  *out = plan->info;
+  return RADON_OK;
+}
+
+int radon_forward(radon_plan plan, const float* d_image, float* d_sino, void* stream) {
+  if (!plan || !d_image || !d_sino) return RADON_INVALID_ARG;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  return status_of(radon::launch_forward(plan->dp, d_image, d_sino, static_cast<cudaStream_t>(stream), hook_of(plan)));
+}
+
+int radon_backproject(radon_plan plan, const float* d_sino, float* d_image, void* stream) {
+  if (!plan || !d_sino || !d_image) return RADON_INVALID_ARG;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  return status_of(radon::launch_backproject(plan->dp, d_sino, d_image, static_cast<cudaStream_t>(stream), hook_of(plan)));
+}
+
+int radon_fbp(radon_plan plan, const float* d_sino, float* d_image, int filter, void* stream) {
+  if (!plan || !d_sino || !d_image) return RADON_INVALID_ARG;
+  if (filter < RADON_FILTER_RAMP || filter > RADON_FILTER_COSINE) return RADON_INVALID_ARG;
+  (void)stream;
+  return RADON_NOT_SUPPORTED;
+}
+
+int radon_forward_host(radon_plan plan, const float* h_image, float* h_sino, void* stream) {
+  if (!plan || !h_image || !h_sino) return RADON_INVALID_ARG;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const radon_plan_info& g = plan->info;
+  cudaError_t e = cudaMemcpyAsync(plan->io_image, h_image, sizeof(float) * static_cast<size_t>(g.N) * g.N,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = radon::launch_forward(plan->dp, plan->io_image, plan->io_sino, st, hook_of(plan));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_sino, plan->io_sino, sizeof(float) * static_cast<size_t>(g.n_angles) * g.n_det,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return status_of(e);
+}
+
+int radon_backproject_host(radon_plan plan, const float* h_sino, float* h_image, void* stream) {
+  if (!plan || !h_sino || !h_image) return RADON_INVALID_ARG;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const radon_plan_info& g = plan->info;
+  cudaError_t e = cudaMemcpyAsync(plan->io_sino, h_sino, sizeof(float) * static_cast<size_t>(g.n_angles) * g.n_det,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = radon::launch_backproject(plan->dp, plan->io_sino, plan->io_image, st, hook_of(plan));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_image, plan->io_image, sizeof(float) * static_cast<size_t>(g.N) * g.N,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return status_of(e);
+}
+
+int radon_profile_enable(radon_plan plan, int enable) {
+  if (!plan) return RADON_INVALID_ARG;
+  plan->prof_on = enable != 0;
+  return RADON_OK;
+}
+
+int radon_profile_read(radon_plan plan, double* ms, int* launches) {
+  if (!plan || !ms || !launches) return RADON_INVALID_ARG;
+  cudaError_t e = plan->prof_err;
+  plan->prof_err = cudaSuccess;
+  for (size_t i = 1; i < plan->prof_used && e == cudaSuccess; ++i) {
+    const int st = plan->prof_stage[i];
+    if (st < 0 || st >= RADON_NUM_STAGES) continue;
+    float t = 0.f;
+    e = cudaEventSynchronize(plan->prof_pool[i]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, plan->prof_pool[i - 1], plan->prof_pool[i]);
+    if (e == cudaSuccess) {
+      ms[st] += t;
+      launches[st] += 1;
+    }
+  }
+  plan->prof_used = 0;
+  return status_of(e);
+}
+
+}  // extern "C"

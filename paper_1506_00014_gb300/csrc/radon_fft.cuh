@@ -1,0 +1,267 @@
+// Block-wide mixed-radix FFT in shared memory (Stockham, self-sorting), FP32 complex.
+//
+// Used for the log-polar convolution of Section 3: a length-N_rho/2 complex transform (the
+// real rho transform of length N_rho) per angular row and a length-n_theta transform per rho
+// frequency.  Twiddles come from FP64-computed tables.  Sizes are 7-smooth; radices are taken
+// from {2, 3, 4, 5, 7, 8, 9}.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace radon {
+
+struct RadixList {
+  int n;
+  int count;
+  int r[24];
+};
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 rot90(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2& a, float2& b, float2& c) {
+  const float s3 = 0.866025403784438646763723170753f;  // sin(2 pi / 3)
+  float2 t1 = cadd(b, c);
+  float2 t2 = make_float2(fmaf(-0.5f, t1.x, a.x), fmaf(-0.5f, t1.y, a.y));
+  float2 t3 = rot90<INV>(cscale(csub(b, c), s3));
+  a = cadd(a, t1);
+  b = cadd(t2, t3);
+  c = csub(t2, t3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d) {
+  float2 s0 = cadd(a, c), d0 = csub(a, c);
+  float2 s1 = cadd(b, d), d1 = rot90<INV>(csub(b, d));
+  a = cadd(s0, s1);
+  c = csub(s0, s1);
+  b = cadd(d0, d1);
+  d = csub(d0, d1);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&v)[R]);
+
+template <>
+__device__ __forceinline__ void dft<2, false>(float2 (&v)[2]) { dft2<false>(v[0], v[1]); }
+template <>
+__device__ __forceinline__ void dft<2, true>(float2 (&v)[2]) { dft2<true>(v[0], v[1]); }
+template <>
+__device__ __forceinline__ void dft<3, false>(float2 (&v)[3]) { dft3<false>(v[0], v[1], v[2]); }
+template <>
+__device__ __forceinline__ void dft<3, true>(float2 (&v)[3]) { dft3<true>(v[0], v[1], v[2]); }
+template <>
+__device__ __forceinline__ void dft<4, false>(float2 (&v)[4]) { dft4<false>(v[0], v[1], v[2], v[3]); }
+template <>
+__device__ __forceinline__ void dft<4, true>(float2 (&v)[4]) { dft4<true>(v[0], v[1], v[2], v[3]); }
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+  const float h = 0.707106781186547524400844362105f;
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  // W8^k, k = 1, 2, 3 (conjugated for the inverse)
+  o1 = INV ? make_float2(h * (o1.x - o1.y), h * (o1.x + o1.y)) : make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));
+  o2 = rot90<INV>(o2);
+  o3 = INV ? make_float2(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+template <>
+__device__ __forceinline__ void dft<8, false>(float2 (&v)[8]) { dft8<false>(v); }
+template <>
+__device__ __forceinline__ void dft<8, true>(float2 (&v)[8]) { dft8<true>(v); }
+
+// Odd prime radix by pairing x_j with x_{R-j}: y_k = x_0 + sum_j (x_j + x_{R-j}) cos(2 pi jk/R)
+//                                                 -/+ i (x_j - x_{R-j}) sin(2 pi jk/R).
+template <int R, bool INV>
+__device__ __forceinline__ void dft_odd(float2 (&v)[R], const float (&cs)[R], const float (&sn)[R]) {
+  constexpr int H = (R - 1) / 2;
+  float2 sp[H], sm[H];
+#pragma unroll
+  for (int j = 1; j <= H; ++j) {
+    sp[j - 1] = cadd(v[j], v[R - j]);
+    sm[j - 1] = csub(v[j], v[R - j]);
+  }
+  float2 y[R];
+  y[0] = v[0];
+#pragma unroll
+  for (int j = 0; j < H; ++j) y[0] = cadd(y[0], sp[j]);
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    float2 re = v[0], im = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+      const int q = (j * k) % R;
+      re.x = fmaf(sp[j - 1].x, cs[q], re.x);
+      re.y = fmaf(sp[j - 1].y, cs[q], re.y);
+      im.x = fmaf(sm[j - 1].x, sn[q], im.x);
+      im.y = fmaf(sm[j - 1].y, sn[q], im.y);
+    }
+    const float2 t = rot90<INV>(im);
+    y[k] = cadd(re, t);
+    y[R - k] = csub(re, t);
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = y[k];
+}
+
+template <>
+__device__ __forceinline__ void dft<5, false>(float2 (&v)[5]) {
+  const float cs[5] = {1.f, 0.309016994374947424102293417183f, -0.809016994374947424102293417183f,
+                       -0.809016994374947424102293417183f, 0.309016994374947424102293417183f};
+  const float sn[5] = {0.f, 0.951056516295153572116439333379f, 0.587785252292473129168705954639f,
+                       -0.587785252292473129168705954639f, -0.951056516295153572116439333379f};
+  dft_odd<5, false>(v, cs, sn);
+}
+template <>
+__device__ __forceinline__ void dft<5, true>(float2 (&v)[5]) {
+  const float cs[5] = {1.f, 0.309016994374947424102293417183f, -0.809016994374947424102293417183f,
+                       -0.809016994374947424102293417183f, 0.309016994374947424102293417183f};
+  const float sn[5] = {0.f, 0.951056516295153572116439333379f, 0.587785252292473129168705954639f,
+                       -0.587785252292473129168705954639f, -0.951056516295153572116439333379f};
+  dft_odd<5, true>(v, cs, sn);
+}
+
+#define RADON_C7 {1.f, 0.623489801858733530525004884004f, -0.222520933956314404288902564497f, \
+                  -0.900968867902419126236102319507f, -0.900968867902419126236102319507f,     \
+                  -0.222520933956314404288902564497f, 0.623489801858733530525004884004f}
+#define RADON_S7 {0.f, 0.781831482468029808708444526674f, 0.974927912181823607018131682994f,  \
+                  0.433883739117558120475768332849f, -0.433883739117558120475768332849f,     \
+                  -0.974927912181823607018131682994f, -0.781831482468029808708444526674f}
+template <>
+__device__ __forceinline__ void dft<7, false>(float2 (&v)[7]) {
+  const float cs[7] = RADON_C7;
+  const float sn[7] = RADON_S7;
+  dft_odd<7, false>(v, cs, sn);
+}
+template <>
+__device__ __forceinline__ void dft<7, true>(float2 (&v)[7]) {
+  const float cs[7] = RADON_C7;
+  const float sn[7] = RADON_S7;
+  dft_odd<7, true>(v, cs, sn);
+}
+
+// Radix 9 = 3 x 3 with internal twiddles W9^(j k), j, k in {1, 2}.
+template <bool INV>
+__device__ __forceinline__ void dft9(float2 (&v)[9]) {
+  // columns: (v0, v3, v6), (v1, v4, v7), (v2, v5, v8)
+  dft3<INV>(v[0], v[3], v[6]);
+  dft3<INV>(v[1], v[4], v[7]);
+  dft3<INV>(v[2], v[5], v[8]);
+  const float2 w1 = make_float2(0.766044443118978035202392650555f, -0.642787609686539326322643409907f);
+  const float2 w2 = make_float2(0.173648177666930348851716626769f, -0.984807753012208059366743024590f);
+  const float2 w4 = make_float2(-0.939692620785908384054109277324f, -0.342020143325668733044099614682f);
+  if (INV) {
+    v[4] = cmulc(v[4], w1);
+    v[7] = cmulc(v[7], w2);
+    v[5] = cmulc(v[5], w2);
+    v[8] = cmulc(v[8], w4);
+  } else {
+    v[4] = cmul(v[4], w1);
+    v[7] = cmul(v[7], w2);
+    v[5] = cmul(v[5], w2);
+    v[8] = cmul(v[8], w4);
+  }
+  dft3<INV>(v[0], v[1], v[2]);
+  dft3<INV>(v[3], v[4], v[5]);
+  dft3<INV>(v[6], v[7], v[8]);
+  // output index 3 * k2 + k1 is stored at position 3 * k1 + k2: transpose
+  float2 t;
+  t = v[1]; v[1] = v[3]; v[3] = t;
+  t = v[2]; v[2] = v[6]; v[6] = t;
+  t = v[5]; v[5] = v[7]; v[7] = t;
+}
+template <>
+__device__ __forceinline__ void dft<9, false>(float2 (&v)[9]) { dft9<false>(v); }
+template <>
+__device__ __forceinline__ void dft<9, true>(float2 (&v)[9]) { dft9<true>(v); }
+
+// One Stockham pass of radix R over `nb` transforms of length n (transform b at src + b * fs).
+template <int R, bool INV>
+__device__ __forceinline__ void stockham_pass(const float2* __restrict__ src, float2* __restrict__ dst, int n,
+                                              int nb, int fs, int Ns, const float2* __restrict__ tw, int tid,
+                                              int nth) {
+  const int nbf = n / R;
+  const int total = nbf * nb;
+  const int tstep = n / (Ns * R);
+  for (int t = tid; t < total; t += nth) {
+    const int b = t / nbf;
+    const int j = t - b * nbf;
+    const int k = j % Ns;
+    const float2* s = src + b * fs;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[j + r * nbf];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tw[r * k * tstep];
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      }
+    }
+    dft<R, INV>(v);
+    float2* d = dst + b * fs + (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[r * Ns] = v[r];
+  }
+}
+
+// Full transform; ping-pongs between a and b, returns the buffer holding the result.
+// All threads of the block must call it.  tw[p] = exp(-2 pi i p / n).
+template <bool INV>
+__device__ float2* fft_block(float2* a, float2* b, int nb, int fs, const RadixList& rl,
+                             const float2* __restrict__ tw, int tid, int nth) {
+  const int n = rl.n;
+  int Ns = 1;
+  for (int st = 0; st < rl.count; ++st) {
+    const int R = rl.r[st];
+    switch (R) {
+      case 2: stockham_pass<2, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
+      case 3: stockham_pass<3, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
+      case 4: stockham_pass<4, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
+      case 5: stockham_pass<5, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
+      case 7: stockham_pass<7, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
+      case 8: stockham_pass<8, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
+      case 9: stockham_pass<9, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
+      default: break;
+    }
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+}  // namespace radon

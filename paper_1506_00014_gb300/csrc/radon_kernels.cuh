@@ -1,0 +1,74 @@
+// Device-side parameter blocks and launch entry points of the log-polar pipeline.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "radon_fft.cuh"
+
+namespace radon {
+
+// Pointers to the plan's FP32 tables and scratch (all device memory) plus the sizes the kernels
+// need.  Filled once at plan creation; passed to kernels by value.
+struct DevPlan {
+  int N, n_angles, n_det, M, interp, N_rho, nh, n_theta, r, nc;
+  int img_pitch;   // padded coefficient image: (N + 2 kPad) columns
+  int sino_pitch;  // padded sinogram coefficients: n_det + 1 + 2 kPad columns
+  int x_pitch;     // complex spectrum rows: >= N_rho/2 + 1
+  int y_pitch;     // real log-polar rows with periodic wrap columns: >= N_rho + 2 kPad
+  int n_eanc, n_ktiles, n_ptiles;
+  int col_group;   // rho frequencies per column CTA (4, 2 or 1: shared memory bound)
+  float inv_drho, inv_dphi, inv_aR, d_s;
+  RadixList rad_rho, rad_th;
+  // tables
+  const float2* tw_rho;
+  const float2* tw_r2c;
+  const float2* tw_th;
+  const float2* k_fwd;
+  const float2* k_bp;
+  const float4* fwd_row;
+  const float4* fwd_m;
+  const float2* fwd_e;
+  const float2* fwd_eanc;
+  const int4* fwd_ang;
+  const int4* fwd_anc;
+  const int2* bp_th;
+  const int2* bp_c;
+  const int2* bp_e;
+  const int4* bp_anc;  // 2 int4 per (m, tile)
+  const float2* bp_m;
+  const float* fir;    // kFirHalf + 1
+  const float* filt;   // FBP transfer function (n_filt_c complex bins) or null
+  // scratch
+  float* coef_img;     // (N + 2 kPad)^2, zero border
+  float* coef_sino;    // n_angles x sino_pitch, zero border
+  float2* xspec;       // M x nh x x_pitch
+  float2* yspec;       // M x (nh + 4) x x_pitch
+  float* ylp;          // M x (nh + 4) x y_pitch
+  float* sino_tmp;     // n_angles x n_det (filtered sinogram for FBP)
+  int n_filt, filt_pitch;  // FBP: padded FFT length along s and spectrum pitch
+  RadixList rad_filt;
+  const float2* tw_filt;
+  const float2* tw_filt_r2c;
+};
+
+// Optional hook called after each kernel launch (stage ids as in radon.h) and once before the
+// first one (stage -1); used for per-stage event timing.
+struct StageHook {
+  void (*mark)(void* ctx, int stage, cudaStream_t st);
+  void* ctx;
+  void operator()(int stage, cudaStream_t st) const {
+    if (mark) mark(ctx, stage, st);
+  }
+};
+
+// Each returns cudaGetLastError() after its launches.
+cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cudaStream_t st, StageHook hook);
+cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook);
+cudaError_t launch_sino_filter(const DevPlan& p, const float* sino, float* out, cudaStream_t st);
+
+// Dynamic shared memory limits are raised once per device.
+cudaError_t configure_kernels(const DevPlan& p);
+
+}  // namespace radon

@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bar (the stated target of this build): relative L2 error <= 1e-5 against the log-polar oracle
+for both R and R#, cubic and linear, on the same seeded inputs.  Sizes span several tiles with
+ragged tails; the full N = 2048 case runs the whole oracle (about a minute of CPU time).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import direct, geometry, kernels, logpolar
+from workloads import ellipse_image, gaussian_image, random_ellipses, random_sinogram, smooth_random_image
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rl():
+    from paper_1506_00014_gb300 import build
+
+    if build.needs_build():
+        build.build()
+    import paper_1506_00014_gb300 as rl
+
+    return rl
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def _gpu_forward(rl, plan, f, stream=None):
+    fd = torch.tensor(np.asarray(f, dtype=np.float32), device="cuda")
+    out = torch.full(plan.sino_shape, float("nan"), dtype=torch.float32, device="cuda")
+    rl.radon_forward(plan, fd, out, stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def _gpu_back(rl, plan, g, stream=None):
+    gd = torch.tensor(np.asarray(g, dtype=np.float32), device="cuda")
+    out = torch.full(plan.image_shape, float("nan"), dtype=torch.float32, device="cuda")
+    rl.radon_backproject(plan, gd, out, stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+CASES = [
+    (128, 128, 192, 3, 3),   # the small CPU configuration
+    (128, 128, 192, 1, 3),   # linear interpolation
+    (96, 100, 150, 3, 4),    # M = 4, ragged angle / detector counts
+    (200, 150, 310, 3, 3),   # image not a multiple of the 16 / 32 tiles
+    (64, 37, 90, 3, 5),      # M = 5, odd angle count
+    (16, 12, 24, 3, 3),      # tiny
+    (16, 5, 20, 1, 3),       # tiny, linear, n_theta_half = 2
+]
+
+
+def _inputs(N, na, nd, seed):
+    img_ell = ellipse_image(N, random_ellipses(10, seed))
+    img_smooth = smooth_random_image(N, seed + 1)
+    rng = np.random.default_rng(seed + 2)
+    img_noise = rng.standard_normal((N, N))
+    sino_noise = random_sinogram(na, nd, seed + 3)
+    return img_ell, img_smooth, img_noise, sino_noise
+
+
+@pytest.mark.parametrize("N,na,nd,interp,M", CASES)
+def test_forward_matches_logpolar_oracle(rl, N, na, nd, interp, M):
+    geo = geometry.make_geometry(N, na, nd, M, interp)
+    plan = rl.radon_plan_create(N, na, nd, interp, M)
+    K = kernels.multiplier(geo, "R")
+    dft = logpolar._Dft(geo)
+    for img in _inputs(N, na, nd, 11)[:3]:
+        ref = logpolar.forward(_f32(img), geo, K=K, dft=dft)
+        got = _gpu_forward(rl, plan, img)
+        assert np.all(np.isfinite(got))
+        assert _rel(got, ref) < TOL, _rel(got, ref)
+
+
+@pytest.mark.parametrize("N,na,nd,interp,M", CASES)
+def test_backprojection_matches_logpolar_oracle(rl, N, na, nd, interp, M):
+    geo = geometry.make_geometry(N, na, nd, M, interp)
+    plan = rl.radon_plan_create(N, na, nd, interp, M)
+    K = kernels.multiplier(geo, "B")
+    dft = logpolar._Dft(geo)
+    sino = _inputs(N, na, nd, 21)[3]
+    th = np.arange(na) * geo.dtheta
+    s = (np.arange(nd) - nd / 2) * geo.ds
+    blobs = [(0.2, -0.1, 0.12, 1.0), (-0.3, 0.25, 0.08, -0.7)]
+    smooth = direct.gaussian_radon(th[:, None], s[None, :], blobs)
+    for g in (sino, smooth):
+        ref = logpolar.backproject(_f32(g), geo, K=K, dft=dft)
+        got = _gpu_back(rl, plan, g)
+        assert np.all(np.isfinite(got))
+        assert _rel(got, ref) < TOL, _rel(got, ref)
+
+
+def test_zero_and_out_of_support_inputs_give_exact_zeros(rl):
+    N, na, nd = 64, 64, 96
+    plan = rl.radon_plan_create(N, na, nd, 3, 3)
+    assert np.count_nonzero(_gpu_forward(rl, plan, np.zeros((N, N)))) == 0
+    outside = np.where(geometry.disc_mask(N), 0.0, 1.0)  # only pixels with |x| >= 1
+    assert np.count_nonzero(_gpu_forward(rl, plan, outside)) == 0
+    dead = np.where(geometry.live_bins(nd)[None, :], 0.0, np.ones((na, nd)))  # only bins with |s| >= 1
+    assert np.count_nonzero(_gpu_back(rl, plan, dead)) == 0
+    # outputs outside the support are exactly zero
+    rf = _gpu_forward(rl, plan, np.ones((N, N)))
+    assert np.count_nonzero(rf[:, ~geometry.live_bins(nd)]) == 0
+    bp = _gpu_back(rl, plan, np.ones((na, nd)))
+    assert np.count_nonzero(bp[~geometry.disc_mask(N)]) == 0
+
+
+def test_deterministic_and_stream_ordered(rl):
+    N, na, nd = 256, 256, 384
+    plan = rl.radon_plan_create(N, na, nd, 3, 3)
+    f = ellipse_image(N, random_ellipses(20, 5))
+    a = _gpu_forward(rl, plan, f)
+    side = torch.cuda.Stream()
+    b = _gpu_forward(rl, plan, f, stream=side)
+    assert np.array_equal(a, b)
+    g = random_sinogram(na, nd, 6)
+    assert np.array_equal(_gpu_back(rl, plan, g), _gpu_back(rl, plan, g, stream=side))
+
+
+def test_host_buffer_entry_points_match_device_ones(rl):
+    N, na, nd = 128, 128, 192
+    plan = rl.radon_plan_create(N, na, nd, 3, 3)
+    f = ellipse_image(N, random_ellipses(10, 1)).astype(np.float32)
+    g = random_sinogram(na, nd, 3).astype(np.float32)
+    hs = np.zeros((na, nd), np.float32)
+    hi = np.zeros((N, N), np.float32)
+    rl.radon_forward_host(plan, f, hs)
+    rl.radon_backproject_host(plan, g, hi)
+    assert np.array_equal(hs.astype(np.float64), _gpu_forward(rl, plan, f))
+    assert np.array_equal(hi.astype(np.float64), _gpu_back(rl, plan, g))
+
+
+def test_invalid_arguments_raise(rl):
+    plan = rl.radon_plan_create(32, 32, 48, 3, 3)
+    with pytest.raises(TypeError):
+        rl.radon_forward(plan, torch.zeros((32, 32)), torch.zeros((32, 48), device="cuda"))
+    with pytest.raises(ValueError):
+        rl.radon_forward(plan, torch.zeros((32, 33), device="cuda"), torch.zeros((32, 48), device="cuda"))
+    lib = rl.load()
+    assert lib.radon_forward(plan.handle, None, None, None) == 1  # RADON_INVALID_ARG
+    assert lib.radon_backproject(None, None, None, None) == 1
+
+
+# ------------------------------------------------------------------ full size (N = 2048)
+
+@pytest.fixture(scope="module")
+def full_geo():
+    return {interp: geometry.make_geometry(2048, 2048, 3072, 3, interp) for interp in (3, 1)}
+
+
+@pytest.mark.parametrize("interp", [3, 1])
+def test_full_size_forward_matches_oracle(rl, full_geo, interp):
+    geo = full_geo[interp]
+    plan = rl.radon_plan_create(2048, 2048, 3072, interp, 3)
+    f = ellipse_image(2048, random_ellipses(50, 2))
+    got = _gpu_forward(rl, plan, f)
+    ref = logpolar.forward(_f32(f), geo)
+    assert _rel(got, ref) < TOL, _rel(got, ref)
+
+
+@pytest.mark.parametrize("interp", [3, 1])
+def test_full_size_backprojection_matches_oracle(rl, full_geo, interp):
+    geo = full_geo[interp]
+    plan = rl.radon_plan_create(2048, 2048, 3072, interp, 3)
+    g = random_sinogram(2048, 3072, 3)
+    got = _gpu_back(rl, plan, g)
+    ref = logpolar.backproject(_f32(g), geo)
+    assert _rel(got, ref) < TOL, _rel(got, ref)
+
+
+# ------------------------------------------------------------------ large sizes: closed forms
+
+@pytest.mark.parametrize("N", [4096, 8192])
+def test_large_sizes_against_closed_forms(rl, N):
+    """At sizes the oracle cannot finish, R of sampled Gaussians must match their analytic
+    Radon transform and R# of the analytic sinogram its closed-form back-projection."""
+    na, nd = N, 3 * N // 2
+    plan = rl.radon_plan_create(N, na, nd, 3, 3)
+    geo = geometry.make_geometry(N, na, nd, 3, 3)
+    blobs = [(0.2, -0.1, 0.12, 1.0), (-0.3, 0.25, 0.08, -0.7), (0.05, 0.5, 0.1, 0.4)]
+    th = np.arange(na) * geo.dtheta
+    s = (np.arange(nd) - nd / 2) * geo.ds
+    sino = direct.gaussian_radon(th[:, None], s[None, :], blobs)
+    sino[:, ~geometry.live_bins(nd)] = 0.0
+    got = _gpu_forward(rl, plan, gaussian_image(N, blobs))
+    assert _rel(got, sino) < 2e-5
+    x = (np.arange(N) - N / 2) * (2.0 / N)
+    bp = np.zeros((N, N))
+    for cx, cy, sg, w in blobs:
+        bp += w * math.sqrt(2 * math.pi) * sg * direct.gaussian_bp(np.hypot(x[None, :] - cx, x[:, None] - cy), sg)
+    bp[~geometry.disc_mask(N)] = 0.0
+    assert _rel(_gpu_back(rl, plan, sino), bp) < 2e-5

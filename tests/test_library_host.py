@@ -1,0 +1,78 @@
+"""Host-side checks of libradon (no GPU): exported symbols, geometry rules and the kernel
+transforms computed by the plan (trapezoid rule + end corrections, Eq. weightsa) against the
+oracle's Gauss-Legendre values."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import geometry, kernels
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1506_00014_gb300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "radon.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(radon_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared_symbols()
+    assert len(declared) >= 11
+    cdll = ctypes.CDLL(lib.library_path())
+    for name in declared:
+        assert hasattr(cdll, name), name
+    assert set(declared) == set(lib.EXPORTED)
+
+
+@pytest.mark.parametrize("args", [(128, 128, 192, 3, 3), (2048, 2048, 3072, 3, 3), (1024, 720, 1536, 3, 3),
+                                  (96, 100, 150, 1, 4), (8192, 8192, 12288, 3, 3), (64, 37, 90, 3, 5)])
+def test_geometry_matches_oracle_rules(lib, args):
+    N, na, nd, interp, M = args
+    g = lib.radon_geometry(N, na, nd, interp, M)
+    o = geometry.make_geometry(N, na, nd, M, interp)
+    assert (g["N_rho"], g["n_theta_half"], g["n_theta"], g["r"]) == (o.N_rho, o.n_th_h, o.n_theta, o.r)
+    for a, b in (("beta", "beta"), ("a_R", "a_R"), ("a_r", "a_r"), ("L", "L"), ("d_phi", "dphi"),
+                 ("d_rho", "drho"), ("d_s", "ds"), ("d_theta", "dtheta")):
+        assert g[a] == pytest.approx(getattr(o, b), rel=1e-15)
+    assert g["n_quad"] >= 8 * g["n_theta"]
+
+
+def test_invalid_geometry_is_rejected(lib):
+    for args in ((7, 8, 8, 3, 3), (6, 8, 8, 3, 3), (16, 8, 8, 2, 3), (16, 8, 8, 3, 2), (16, 1, 8, 3, 3)):
+        with pytest.raises(lib.RadonError):
+            lib.radon_geometry(*args)
+
+
+@pytest.mark.parametrize("N,na,nd,M", [(64, 64, 96, 3), (128, 128, 192, 3), (256, 256, 384, 4)])
+def test_plan_kernel_transforms_match_oracle(lib, N, na, nd, M):
+    o = geometry.make_geometry(N, na, nd, M)
+    for which, key in ((0, "R"), (1, "B")):
+        plan_k = lib.radon_kernel_quadrant(N, na, nd, M, which)
+        ref = kernels.kernel_quadrant(o, key)
+        assert plan_k.shape == ref.shape
+        assert np.max(np.abs(plan_k - ref)) < 1e-8 * np.max(np.abs(ref))
+
+
+def test_end_correction_weights_are_exact_to_degree_six():
+    """Eq. weightsa: with f(a + j h) the moments sum_j c_j j^p / 120960 equal the
+    Euler-Maclaurin end terms 0, 1/12, 0, -1/720 * 3!, 0, 1/30240 * 5!, 0."""
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "end_correction_weights.txt"))
+            if l.strip() and not l.startswith("#")]
+    c = np.array([float(v) for _, v in rows])
+    j = np.arange(7.0)
+    from math import factorial
+    expect = [0.0, 1 / 12, 0.0, -factorial(3) / 720, 0.0, factorial(5) / 30240, 0.0]
+    for p in range(7):
+        assert np.sum(c * j**p) / 120960 == pytest.approx(expect[p], abs=1e-15)
