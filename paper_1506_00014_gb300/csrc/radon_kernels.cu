@@ -484,8 +484,14 @@ void launch_columns_and_inverse(const DevPlan& p, const float2* kern, cudaStream
 }  // namespace
 
 cudaError_t configure_kernels(const DevPlan& p) {
+  // The limit is a per-function attribute shared by every plan on the device: raise it to the
+  // device's opt-in maximum (never to one plan's need, which a later, smaller plan would lower).
   cudaError_t e;
-  const int rs = static_cast<int>(rows_smem(p)), cs = static_cast<int>(cols_smem(p));
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  if (rows_smem(p) > static_cast<size_t>(optin) || cols_smem(p) > static_cast<size_t>(optin)) return cudaErrorInvalidValue;
+  const int rs = optin, cs = optin;
   if ((e = cudaFuncSetAttribute(k_rows_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_rows_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;

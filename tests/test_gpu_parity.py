@@ -133,6 +133,18 @@ def test_deterministic_and_stream_ordered(rl):
     assert np.array_equal(_gpu_back(rl, plan, g), _gpu_back(rl, plan, g, stream=side))
 
 
+def test_plans_of_different_sizes_coexist(rl):
+    """A plan stays usable after a smaller (or larger) plan is created on the same device."""
+    big = rl.radon_plan_create(256, 256, 384, 3, 3)
+    small = rl.radon_plan_create(32, 32, 48, 3, 3)
+    f_big = ellipse_image(256, random_ellipses(10, 4))
+    geo = geometry.make_geometry(256, 256, 384, 3, 3)
+    ref = logpolar.forward(_f32(f_big), geo)
+    assert _rel(_gpu_forward(rl, big, f_big), ref) < TOL
+    assert np.all(np.isfinite(_gpu_forward(rl, small, ellipse_image(32, random_ellipses(3, 4)))))
+    assert _rel(_gpu_forward(rl, big, f_big), ref) < TOL
+
+
 def test_host_buffer_entry_points_match_device_ones(rl):
     N, na, nd = 128, 128, 192
     plan = rl.radon_plan_create(N, na, nd, 3, 3)
