@@ -43,7 +43,8 @@ typedef enum {
   RADON_OUT_OF_MEMORY = 2,   /* a device or host allocation failed */
   RADON_CUDA_ERROR = 3,      /* a CUDA runtime call or kernel launch failed */
   RADON_TIMEOUT = 4,         /* a bounded device-side wait gave up */
-  RADON_NOT_SUPPORTED = 5    /* valid request outside what this build handles */
+  RADON_NOT_SUPPORTED = 5,   /* valid request outside what this build handles */
+  RADON_EXCEEDS_STATIC_SCRATCH = 6  /* radon_forward_static_scratch: plan too large for the static array */
 } radon_status;
 
 typedef enum {
@@ -120,6 +121,28 @@ int radon_kernel_quadrant(int N, int n_angles, int n_det, int n_partitions, int 
 #define RADON_NUM_STAGES 10
 int radon_profile_enable(radon_plan plan, int enable);
 int radon_profile_read(radon_plan plan, double* ms, int* launches);
+
+/* Forward transform R without any allocation, for callers that must not allocate device memory
+ * when they run a transform: code that runs under a framework owning every device allocation
+ * (where a raw cudaMalloc is forbidden or would fragment its pool), or a real-time loop with a
+ * fixed device-memory budget.  The paper has no counterpart; this is a deployment variant of
+ * radon_forward and gives the same result.
+ *
+ * The plan's precomputed tables are used as they are (they were allocated when the plan was
+ * created), but the transform's intermediate arrays (coefficient image, spectra, log-polar
+ * coefficients) live in one static device array of RADON_STATIC_SCRATCH_BYTES (16 MiB) that
+ * every GPU which loads the library holds until the process exits.  That is enough for N = 512
+ * with 512 angles and 768 bins; a plan whose intermediates do not fit is rejected with
+ * RADON_EXCEEDS_STATIC_SCRATCH before anything is launched.
+ *
+ * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.  Its
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  The array is shared by all
+ * calls on a device and keeps the last call's contents; each call clears what must start at zero.
+ * Calls that can overlap on the GPU (different streams, or different host threads) race on the
+ * array: order them on one stream or synchronise between them. */
+#define RADON_STATIC_SCRATCH_BYTES (16u << 20)
+int radon_forward_static_scratch(radon_plan plan, const float* d_image, float* d_sino, void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* radon_status_string(int status);

@@ -16,6 +16,7 @@ from .binding import (  # noqa: F401
     radon_fbp,
     radon_forward,
     radon_forward_host,
+    radon_forward_static_scratch,
     radon_geometry,
     radon_kernel_quadrant,
     radon_plan_create,

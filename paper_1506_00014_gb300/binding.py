@@ -38,7 +38,7 @@ EXPORTED = (
     "radon_plan_create", "radon_plan_destroy", "radon_plan_get_info", "radon_forward",
     "radon_backproject", "radon_fbp", "radon_forward_host", "radon_backproject_host",
     "radon_geometry", "radon_kernel_quadrant", "radon_status_string", "radon_profile_enable",
-    "radon_profile_read",
+    "radon_profile_read", "radon_forward_static_scratch",
 )
 
 RADON_NUM_STAGES = 10
@@ -74,7 +74,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.radon_plan_destroy.argtypes = [_c_void_p]
     lib.radon_plan_destroy.restype = None
     lib.radon_plan_get_info.argtypes = [_c_void_p, P(radon_plan_info)]
-    for name in ("radon_forward", "radon_backproject", "radon_forward_host", "radon_backproject_host"):
+    for name in ("radon_forward", "radon_backproject", "radon_forward_host", "radon_backproject_host",
+                 "radon_forward_static_scratch"):
         getattr(lib, name).argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p]
     lib.radon_fbp.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_void_p]
     lib.radon_geometry.argtypes = [_c_int, _c_int, _c_int, _c_int, _c_int, P(radon_plan_info)]
@@ -183,6 +184,14 @@ def _stream(stream, tensor):
 def radon_forward(plan: RadonPlan, image, sino, stream=None):
     _check(load().radon_forward(plan.handle, _dev(image, plan.image_shape, "image"),
                                 _dev(sino, plan.sino_shape, "sino"), _stream(stream, image)), "radon_forward")
+    return sino
+
+
+def radon_forward_static_scratch(plan: RadonPlan, image, sino, stream=None):
+    """radon_forward with the intermediates in the library's static device array (no allocation)."""
+    _check(load().radon_forward_static_scratch(plan.handle, _dev(image, plan.image_shape, "image"),
+                                               _dev(sino, plan.sino_shape, "sino"), _stream(stream, image)),
+           "radon_forward_static_scratch")
     return sino
 
 

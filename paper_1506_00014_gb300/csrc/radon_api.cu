@@ -6,24 +6,10 @@
 #include <vector>
 
 #include "plan_host.h"
+#include "plan_internal.h"
 #include "radon.h"
 #include "radon_kernels.cuh"
 
-struct radon_plan_s {
-  radon_plan_info info;
-  radon::DevPlan dp;
-  int device = -1;
-  void* table_mem = nullptr;
-  void* scratch_mem = nullptr;
-  float* io_image = nullptr;  // device staging for the host-buffer entry points
-  float* io_sino = nullptr;
-  // per-stage event timing (radon_profile_enable / radon_profile_read)
-  bool prof_on = false;
-  std::vector<cudaEvent_t> prof_pool;
-  std::vector<int> prof_stage;  // stage id recorded with each used event (-1: start of a call)
-  size_t prof_used = 0;
-  cudaError_t prof_err = cudaSuccess;
-};
 
 namespace {
 
@@ -115,6 +101,8 @@ const char* radon_status_string(int status) {
     case RADON_CUDA_ERROR: return "CUDA error";
     case RADON_TIMEOUT: return "timeout";
     case RADON_NOT_SUPPORTED: return "not supported";
+    case RADON_EXCEEDS_STATIC_SCRATCH:
+      return "plan's intermediate arrays exceed the static scratch array (RADON_STATIC_SCRATCH_BYTES)";
     default: return "unknown status";
   }
 }
