@@ -1,6 +1,7 @@
 // C ABI of libradon (declared in include/radon.h): plan lifecycle and transform entry points.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -51,10 +52,25 @@ class TablePacker {
   size_t total_ = 0;
 };
 
-void copy_radices(const radon::Radices& r, radon::RadixList* out) {
+unsigned magic_of(int d) { return d == 1 ? 0u : static_cast<unsigned>((0x100000000ULL + d - 1) / d); }
+
+bool copy_radices(const radon::Radices& r, int max_batch, radon::RadixList* out) {
+  if (r.count > 16 || static_cast<long long>(r.n) * max_batch >= (1 << 15)) return false;
+  std::memset(out, 0, sizeof(*out));
   out->n = r.n;
   out->count = r.count;
-  for (int i = 0; i < 24; ++i) out->r[i] = i < r.count ? r.r[i] : 0;
+  int Ns = 1;
+  for (int i = 0; i < r.count; ++i) {
+    radon::FftPass& ps = out->p[i];
+    ps.R = r.r[i];
+    ps.Ns = Ns;
+    ps.nbf = r.n / ps.R;
+    ps.tstep = r.n / (Ns * ps.R);
+    ps.m_nbf = magic_of(ps.nbf);
+    ps.m_ns = magic_of(Ns);
+    Ns *= ps.R;
+  }
+  return true;
 }
 
 void prof_mark(void* ctx, int stage, cudaStream_t st) {
@@ -126,6 +142,9 @@ void radon_plan_destroy(radon_plan plan) {
   if (!plan) return;
   cudaDeviceSynchronize();
   for (cudaEvent_t ev : plan->prof_pool) cudaEventDestroy(ev);
+  if (plan->dp.tex_img) cudaDestroyTextureObject(plan->dp.tex_img);
+  if (plan->dp.surf_img) cudaDestroySurfaceObject(plan->dp.surf_img);
+  if (plan->img_array) cudaFreeArray(plan->img_array);
   cudaFree(plan->table_mem);
   cudaFree(plan->scratch_mem);
   delete plan;
@@ -167,10 +186,20 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.n_eanc = (g.N_rho + radon::kETile - 1) / radon::kETile;
   d.n_ktiles = (n_det + radon::kKTile - 1) / radon::kKTile;
   d.n_ptiles = (N + radon::kPTile - 1) / radon::kPTile;
-  d.col_group = 4;
-  while (d.col_group > 1 && 2 * static_cast<size_t>(d.col_group) * g.n_theta * sizeof(float2) > (200u << 10)) d.col_group /= 2;
-  if (2 * static_cast<size_t>(d.col_group) * g.n_theta * sizeof(float2) > (220u << 10) ||
-      2 * static_cast<size_t>(g.N_rho / 2) * sizeof(float2) > (220u << 10)) {
+  d.live_lo = n_det;
+  d.live_hi = -1;
+  for (int k = 0; k < n_det; ++k) {  // |s_k| < 1  <=>  2 (2k - n_det)^2 < n_det^2
+    const long long v = 2LL * k - n_det;
+    if (2 * v * v < static_cast<long long>(n_det) * n_det) {
+      if (k < d.live_lo) d.live_lo = k;
+      d.live_hi = k;
+    }
+  }
+  d.col_group = 4;  // shared memory of a column CTA: (2 G + 1) n_theta complex
+  while (d.col_group > 1 && (2 * static_cast<size_t>(d.col_group) + 1) * g.n_theta * sizeof(float2) > (60u << 10))
+    d.col_group /= 2;
+  if ((2 * static_cast<size_t>(d.col_group) + 1) * g.n_theta * sizeof(float2) > (220u << 10) ||
+      3 * static_cast<size_t>(g.N_rho / 2) * sizeof(float2) > (220u << 10)) {
     delete p;
     return RADON_NOT_SUPPORTED;
   }
@@ -178,8 +207,10 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.inv_dphi = static_cast<float>(1.0 / g.d_phi);
   d.inv_aR = static_cast<float>(1.0 / g.a_R);
   d.d_s = static_cast<float>(g.d_s);
-  copy_radices(t.rad_rho, &d.rad_rho);
-  copy_radices(t.rad_th, &d.rad_th);
+  if (!copy_radices(t.rad_rho, 1, &d.rad_rho) || !copy_radices(t.rad_th, d.col_group, &d.rad_th)) {
+    delete p;
+    return RADON_NOT_SUPPORTED;
+  }
 
   TablePacker tp;
   const size_t o_tw_rho = tp.add(t.tw_rho), o_tw_r2c = tp.add(t.tw_r2c), o_tw_th = tp.add(t.tw_th);
@@ -241,6 +272,32 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   p->io_sino = reinterpret_cast<float*>(sb + s_io_sino);
   p->info.device_bytes = tp.total() + sc;
 
+  // Coefficient image as a texture over a CUDA array (forward sampling reads it with
+  // tex2Dgather); the pre-filter writes it through a surface.
+  {
+    cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
+    e = cudaMallocArray(&p->img_array, &fd, N, N, cudaArraySurfaceLoadStore);
+    cudaResourceDesc rd;
+    std::memset(&rd, 0, sizeof(rd));
+    rd.resType = cudaResourceTypeArray;
+    rd.res.array.array = p->img_array;
+    cudaTextureDesc td;
+    std::memset(&td, 0, sizeof(td));
+    td.addressMode[0] = cudaAddressModeBorder;
+    td.addressMode[1] = cudaAddressModeBorder;
+    td.filterMode = cudaFilterModePoint;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    if (e == cudaSuccess) e = cudaCreateTextureObject(&d.tex_img, &rd, &td, nullptr);
+    if (e == cudaSuccess) e = cudaCreateSurfaceObject(&d.surf_img, &rd);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      radon_plan_destroy(p);
+      return status_of(e);
+    }
+    d.use_tex = 1;
+    p->info.device_bytes += sizeof(float) * static_cast<size_t>(N) * N;
+  }
   e = radon::configure_kernels(d);
   if (e != cudaSuccess) {
     radon_plan_destroy(p);

@@ -10,11 +10,23 @@
 
 namespace radon {
 
+// One Stockham pass: radix R after Ns points have been combined; nbf = n / R butterflies per
+// transform, tstep = n / (Ns R).  m_nbf / m_ns are ceil(2^32 / d) for the divisions by nbf and
+// Ns (exact for numerators and divisors below 2^15; 0 when the divisor is 1).
+struct FftPass {
+  int R, Ns, nbf, tstep;
+  unsigned m_nbf, m_ns;
+};
+
 struct RadixList {
   int n;
   int count;
-  int r[24];
+  FftPass p[16];
 };
+
+__device__ __forceinline__ int fast_div(int v, int d, unsigned m) {
+  return d == 1 ? v : static_cast<int>(__umulhi(static_cast<unsigned>(v), m));
+}
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -207,17 +219,18 @@ template <>
 __device__ __forceinline__ void dft<9, true>(float2 (&v)[9]) { dft9<true>(v); }
 
 // One Stockham pass of radix R over `nb` transforms of length n (transform b at src + b * fs).
+// tw[p] = exp(-2 pi i p / n), normally staged in shared memory.
 template <int R, bool INV>
 __device__ __forceinline__ void stockham_pass(const float2* __restrict__ src, float2* __restrict__ dst, int n,
-                                              int nb, int fs, int Ns, const float2* __restrict__ tw, int tid,
-                                              int nth) {
-  const int nbf = n / R;
+                                              int nb, int fs, const FftPass& ps, const float2* __restrict__ tw,
+                                              int tid, int nth) {
+  const int nbf = ps.nbf, Ns = ps.Ns, tstep = ps.tstep;
   const int total = nbf * nb;
-  const int tstep = n / (Ns * R);
   for (int t = tid; t < total; t += nth) {
-    const int b = t / nbf;
+    const int b = fast_div(t, nbf, ps.m_nbf);
     const int j = t - b * nbf;
-    const int k = j % Ns;
+    const int q = fast_div(j, Ns, ps.m_ns);
+    const int k = j - q * Ns;
     const float2* s = src + b * fs;
     float2 v[R];
 #pragma unroll
@@ -230,38 +243,41 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ src, fl
       }
     }
     dft<R, INV>(v);
-    float2* d = dst + b * fs + (j - k) * R + k;
+    float2* d = dst + b * fs + q * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) d[r * Ns] = v[r];
   }
 }
 
 // Full transform; ping-pongs between a and b, returns the buffer holding the result.
-// All threads of the block must call it.  tw[p] = exp(-2 pi i p / n).
+// All threads of the block must call it.
 template <bool INV>
 __device__ float2* fft_block(float2* a, float2* b, int nb, int fs, const RadixList& rl,
                              const float2* __restrict__ tw, int tid, int nth) {
   const int n = rl.n;
-  int Ns = 1;
   for (int st = 0; st < rl.count; ++st) {
-    const int R = rl.r[st];
-    switch (R) {
-      case 2: stockham_pass<2, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
-      case 3: stockham_pass<3, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
-      case 4: stockham_pass<4, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
-      case 5: stockham_pass<5, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
-      case 7: stockham_pass<7, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
-      case 8: stockham_pass<8, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
-      case 9: stockham_pass<9, INV>(a, b, n, nb, fs, Ns, tw, tid, nth); break;
+    const FftPass& ps = rl.p[st];
+    switch (ps.R) {
+      case 2: stockham_pass<2, INV>(a, b, n, nb, fs, ps, tw, tid, nth); break;
+      case 3: stockham_pass<3, INV>(a, b, n, nb, fs, ps, tw, tid, nth); break;
+      case 4: stockham_pass<4, INV>(a, b, n, nb, fs, ps, tw, tid, nth); break;
+      case 5: stockham_pass<5, INV>(a, b, n, nb, fs, ps, tw, tid, nth); break;
+      case 7: stockham_pass<7, INV>(a, b, n, nb, fs, ps, tw, tid, nth); break;
+      case 8: stockham_pass<8, INV>(a, b, n, nb, fs, ps, tw, tid, nth); break;
+      case 9: stockham_pass<9, INV>(a, b, n, nb, fs, ps, tw, tid, nth); break;
       default: break;
     }
     __syncthreads();
     float2* t = a;
     a = b;
     b = t;
-    Ns *= R;
   }
   return a;
+}
+
+// Copy an n-entry table into shared memory (all threads; caller synchronises).
+__device__ __forceinline__ void stage_table(float2* dst, const float2* __restrict__ src, int n, int tid, int nth) {
+  for (int i = tid; i < n; i += nth) dst[i] = __ldg(src + i);
 }
 
 }  // namespace radon

@@ -26,8 +26,6 @@ namespace radon {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPfTile = 32;
-constexpr int kPfWide = kPfTile + 2 * kFirHalf;
 
 __device__ __forceinline__ int odd_ext(int p, int n, float* sgn) {
   // extension of [0, n) that is odd about -1 and about n (period 2n + 2)
@@ -49,11 +47,6 @@ __device__ __forceinline__ int odd_ext(int p, int n, float* sgn) {
 __device__ __forceinline__ bool in_disc(int i, int j, int N) {
   const long long di = 2LL * i - N, dj = 2LL * j - N;
   return di * di + dj * dj < static_cast<long long>(N) * N;
-}
-
-__device__ __forceinline__ bool live_bin(int k, int nd) {
-  const long long v = 2LL * k - nd;
-  return 2 * v * v < static_cast<long long>(nd) * nd;
 }
 
 // Cubic B-spline weights of taps k-1, k, k+1, k+2 at fractional offset a (Eq. wsumn).
@@ -84,111 +77,126 @@ __device__ __forceinline__ void df_mul_add(float ah, float al, float bh, float b
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // ------------------------------------------------------------------------------------------
-// Pre-filter of the image: mask to the unit disc, separable truncated FIR with the odd
-// (zero-boundary) extension.  interp == 1: masked copy.
-__global__ void __launch_bounds__(kThreads) k_prefilter_image(DevPlan p, const float* __restrict__ f) {
-  __shared__ float s_in[kPfWide][kPfWide + 1];
-  __shared__ float s_mid[kPfWide][kPfTile + 1];
-  const int N = p.N;
-  const int tx0 = blockIdx.x * kPfTile, ty0 = blockIdx.y * kPfTile;
-  const int tid = threadIdx.x;
-  float q[kFirHalf + 1];
-#pragma unroll
-  for (int n = 0; n <= kFirHalf; ++n) q[n] = __ldg(p.fir + n);
-  for (int idx = tid; idx < kPfWide * kPfWide; idx += kThreads) {
-    const int ly = idx / kPfWide, lx = idx - (idx / kPfWide) * kPfWide;
-    float sy, sx;
-    const int gy = odd_ext(ty0 + ly - kFirHalf, N, &sy);
-    const int gx = odd_ext(tx0 + lx - kFirHalf, N, &sx);
-    float v = 0.f;
-    const float sg = sy * sx;
-    if (sg != 0.f && in_disc(gy, gx, N)) v = sg * __ldg(f + static_cast<size_t>(gy) * N + gx);
-    s_in[ly][lx] = v;
-  }
-  __syncthreads();
-  if (p.interp == 1) {
-    for (int idx = tid; idx < kPfTile * kPfTile; idx += kThreads) {
-      const int ly = idx / kPfTile, lx = idx % kPfTile;
-      const int gy = ty0 + ly, gx = tx0 + lx;
-      if (gy < N && gx < N)
-        p.coef_img[static_cast<size_t>(gy + kPad) * p.img_pitch + gx + kPad] = s_in[ly + kFirHalf][lx + kFirHalf];
-    }
-    return;
-  }
-  for (int idx = tid; idx < kPfWide * kPfTile; idx += kThreads) {
-    const int ly = idx / kPfTile, lx = idx % kPfTile;
-    const float* row = &s_in[ly][lx + kFirHalf];
-    float acc = q[0] * row[0];
-#pragma unroll
-    for (int n = 1; n <= kFirHalf; ++n) acc = fmaf(q[n], row[-n] + row[n], acc);
-    s_mid[ly][lx] = acc;
-  }
-  __syncthreads();
-  for (int idx = tid; idx < kPfTile * kPfTile; idx += kThreads) {
-    const int ly = idx / kPfTile, lx = idx % kPfTile;
-    const int gy = ty0 + ly, gx = tx0 + lx;
-    if (gy >= N || gx >= N) continue;
-    float acc = q[0] * s_mid[ly + kFirHalf][lx];
-#pragma unroll
-    for (int n = 1; n <= kFirHalf; ++n)
-      acc = fmaf(q[n], s_mid[ly + kFirHalf - n][lx] + s_mid[ly + kFirHalf + n][lx], acc);
-    p.coef_img[static_cast<size_t>(gy + kPad) * p.img_pitch + gx + kPad] = acc;
-  }
-}
+// Pre-filters.  One CTA computes a kPfRows x kPfCols tile of coefficients from the tile plus a
+// kFirHalf halo, staged in shared memory; the FIR runs along rows and then along columns, each
+// thread producing kPfSeg consecutive outputs from a register window.  Tiles whose halo stays
+// inside the array read it directly; border tiles map every index through the extension.
 
-// Pre-filter of the sinogram on the (2 n_angles) x (n_det + 1) extension: theta periodic with
-// g(theta + pi, s) = g(theta, -s) (bin k <-> n_det - k), s with the zero boundary; bins with
-// |s| >= 1 are zero.  Writes the first n_angles rows (the rest follow by the flip).
-__global__ void __launch_bounds__(kThreads) k_prefilter_sino(DevPlan p, const float* __restrict__ g) {
-  __shared__ float s_in[kPfWide][kPfWide + 1];
-  __shared__ float s_mid[kPfWide][kPfTile + 1];
-  const int na = p.n_angles, nd = p.n_det, ne = nd + 1;
-  const int tx0 = blockIdx.x * kPfTile, ty0 = blockIdx.y * kPfTile;
-  const int tid = threadIdx.x;
-  float q[kFirHalf + 1];
-#pragma unroll
-  for (int n = 0; n <= kFirHalf; ++n) q[n] = __ldg(p.fir + n);
-  for (int idx = tid; idx < kPfWide * kPfWide; idx += kThreads) {
-    const int ly = idx / kPfWide, lx = idx - (idx / kPfWide) * kPfWide;
-    int a2 = (ty0 + ly - kFirHalf) % (2 * na);
+constexpr int kPfRows = 32, kPfCols = 64, kPfSeg = 8;
+constexpr int kPfInR = kPfRows + 2 * kFirHalf, kPfInC = kPfCols + 2 * kFirHalf;
+
+// Masked image; extension odd about -1 and N in both axes (zero boundary, Eq. Qfrecursive).
+struct ImageSource {
+  const float* __restrict__ f;
+  int N;
+  __device__ __forceinline__ bool interior(int r0, int r1, int c0, int c1) const {
+    return r0 >= 0 && r1 <= N && c0 >= 0 && c1 <= N;
+  }
+  __device__ __forceinline__ float direct(int r, int c) const {
+    const int dr = 2 * r - N, dc = 2 * c - N;  // |x| < 1  <=>  dr^2 + dc^2 < N^2 (N <= 32768)
+    const unsigned d2 = static_cast<unsigned>(dr * dr) + static_cast<unsigned>(dc * dc);
+    return d2 < static_cast<unsigned>(N) * static_cast<unsigned>(N) ? __ldg(f + static_cast<size_t>(r) * N + c) : 0.f;
+  }
+  __device__ __forceinline__ float extended(int r, int c) const {
+    float sr, sc;
+    const int rr = odd_ext(r, N, &sr);
+    const int cc = odd_ext(c, N, &sc);
+    const float sg = sr * sc;
+    return sg != 0.f ? sg * direct(rr, cc) : 0.f;
+  }
+};
+
+// Sinogram rows a (theta periodic over 2 n_angles, rows >= n_angles flipped k -> n_det - k) and
+// columns k in [0, n_det] (the extra k = n_det is zero); zero boundary in k; dead bins zero.
+struct SinoSource {
+  const float* __restrict__ g;
+  int na, nd, live_lo, live_hi;
+  __device__ __forceinline__ bool interior(int r0, int r1, int c0, int c1) const {
+    return r0 >= 0 && r1 <= na && c0 >= 0 && c1 <= nd + 1;
+  }
+  __device__ __forceinline__ float direct(int a, int k) const {
+    return (k >= live_lo && k <= live_hi) ? __ldg(g + static_cast<size_t>(a) * nd + k) : 0.f;
+  }
+  __device__ __forceinline__ float extended(int r, int c) const {
+    int a2 = r % (2 * na);
     if (a2 < 0) a2 += 2 * na;
     const bool flip = a2 >= na;
-    const int arow = flip ? a2 - na : a2;
     float sc;
-    const int qc = odd_ext(tx0 + lx - kFirHalf, ne, &sc);
-    const int c = flip ? nd - qc : qc;
-    float v = 0.f;
-    if (sc != 0.f && c < nd && live_bin(c, nd)) v = sc * __ldg(g + static_cast<size_t>(arow) * nd + c);
-    s_in[ly][lx] = v;
+    const int q = odd_ext(c, nd + 1, &sc);
+    if (sc == 0.f) return 0.f;
+    const int k = flip ? nd - q : q;
+    return sc * direct(flip ? a2 - na : a2, k);
+  }
+};
+
+template <class Src>
+__global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int n_rows, int n_cols,
+                                                        float* __restrict__ out, int out_pitch, int out_r0,
+                                                        cudaSurfaceObject_t surf) {
+  __shared__ float s_in[kPfInR][kPfInC + 1];
+  __shared__ float s_mid[kPfInR][kPfCols + 1];
+  const int r0 = blockIdx.y * kPfRows - kFirHalf, c0 = blockIdx.x * kPfCols - kFirHalf;
+  const int tid = threadIdx.x;
+  if (src.interior(r0, r0 + kPfInR, c0, c0 + kPfInC)) {
+    for (int idx = tid; idx < kPfInR * kPfInC; idx += kThreads) {
+      const int ly = idx / kPfInC, lx = idx - ly * kPfInC;
+      s_in[ly][lx] = src.direct(r0 + ly, c0 + lx);
+    }
+  } else {
+    for (int idx = tid; idx < kPfInR * kPfInC; idx += kThreads) {
+      const int ly = idx / kPfInC, lx = idx - ly * kPfInC;
+      s_in[ly][lx] = src.extended(r0 + ly, c0 + lx);
+    }
   }
   __syncthreads();
-  if (p.interp == 1) {
-    for (int idx = tid; idx < kPfTile * kPfTile; idx += kThreads) {
-      const int ly = idx / kPfTile, lx = idx % kPfTile;
-      const int a = ty0 + ly, c = tx0 + lx;
-      if (a < na && c < ne)
-        p.coef_sino[static_cast<size_t>(a) * p.sino_pitch + c + kPad] = s_in[ly + kFirHalf][lx + kFirHalf];
+  const int orow = blockIdx.y * kPfRows, ocol = blockIdx.x * kPfCols;
+  if (p.interp == 1) {  // linear interpolation uses the masked samples themselves
+    for (int idx = tid; idx < kPfRows * kPfCols; idx += kThreads) {
+      const int ly = idx / kPfCols, lx = idx - ly * kPfCols;
+      if (orow + ly < n_rows && ocol + lx < n_cols) {
+        const float v = s_in[ly + kFirHalf][lx + kFirHalf];
+        out[static_cast<size_t>(orow + ly + out_r0) * out_pitch + ocol + lx + kPad] = v;
+        if (surf) surf2Dwrite(v, surf, (ocol + lx) * static_cast<int>(sizeof(float)), orow + ly);
+      }
     }
     return;
   }
-  for (int idx = tid; idx < kPfWide * kPfTile; idx += kThreads) {
-    const int ly = idx / kPfTile, lx = idx % kPfTile;
-    const float* row = &s_in[ly][lx + kFirHalf];
-    float acc = q[0] * row[0];
+  float q[kFirHalf + 1];
 #pragma unroll
-    for (int n = 1; n <= kFirHalf; ++n) acc = fmaf(q[n], row[-n] + row[n], acc);
-    s_mid[ly][lx] = acc;
+  for (int n = 0; n <= kFirHalf; ++n) q[n] = __ldg(p.fir + n);
+  // along rows: kPfInR rows x (kPfCols / kPfSeg) segments
+  for (int task = tid; task < kPfInR * (kPfCols / kPfSeg); task += kThreads) {
+    const int ly = task / (kPfCols / kPfSeg), sx = (task - ly * (kPfCols / kPfSeg)) * kPfSeg;
+    float w[kPfSeg + 2 * kFirHalf];
+#pragma unroll
+    for (int t = 0; t < kPfSeg + 2 * kFirHalf; ++t) w[t] = s_in[ly][sx + t];
+#pragma unroll
+    for (int t = 0; t < kPfSeg; ++t) {
+      float acc = q[0] * w[t + kFirHalf];
+#pragma unroll
+      for (int n = 1; n <= kFirHalf; ++n) acc = fmaf(q[n], w[t + kFirHalf - n] + w[t + kFirHalf + n], acc);
+      s_mid[ly][sx + t] = acc;
+    }
   }
   __syncthreads();
-  for (int idx = tid; idx < kPfTile * kPfTile; idx += kThreads) {
-    const int ly = idx / kPfTile, lx = idx % kPfTile;
-    const int a = ty0 + ly, c = tx0 + lx;
-    if (a >= na || c >= ne) continue;
-    float acc = q[0] * s_mid[ly + kFirHalf][lx];
+  // along columns: kPfCols columns x (kPfRows / kPfSeg) segments
+  for (int task = tid; task < kPfCols * (kPfRows / kPfSeg); task += kThreads) {
+    const int lx = task % kPfCols, sy = (task / kPfCols) * kPfSeg;
+    float w[kPfSeg + 2 * kFirHalf];
 #pragma unroll
-    for (int n = 1; n <= kFirHalf; ++n)
-      acc = fmaf(q[n], s_mid[ly + kFirHalf - n][lx] + s_mid[ly + kFirHalf + n][lx], acc);
-    p.coef_sino[static_cast<size_t>(a) * p.sino_pitch + c + kPad] = acc;
+    for (int t = 0; t < kPfSeg + 2 * kFirHalf; ++t) w[t] = s_mid[sy + t][lx];
+    const int gc = ocol + lx;
+#pragma unroll
+    for (int t = 0; t < kPfSeg; ++t) {
+      float acc = q[0] * w[t + kFirHalf];
+#pragma unroll
+      for (int n = 1; n <= kFirHalf; ++n) acc = fmaf(q[n], w[t + kFirHalf - n] + w[t + kFirHalf + n], acc);
+      const int gr = orow + sy + t;
+      if (gr < n_rows && gc < n_cols) {
+        out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = acc;
+        if (surf) surf2Dwrite(acc, surf, gc * static_cast<int>(sizeof(float)), gr);
+      }
+    }
   }
 }
 
@@ -222,94 +230,174 @@ __device__ __forceinline__ float sample_image(const DevPlan& p, int ic, float ac
 }
 
 // Forward: h(phi_j, rho_i) = e^rho_i / r * sum_q f~(T_m^{-1}(e^rho_i (cos phi_jq, sin phi_jq))).
-// Coordinates: a double-float anchor per 32-sample rho tile plus an FP32 offset.
-__device__ void sample_row_forward(const DevPlan& p, int m, int jj, float* __restrict__ h) {
+//
+// Coordinates: for each sub-angle q and each 32-sample rho tile, a double-float anchor
+// col/row = e^rho_anchor * (cos, sin)(psi_q) * N / (2 a_R) + offset, computed once per CTA into
+// shared memory as (integer, fraction); each sample adds the FP32 offset (e^rho_i - e^rho_anchor)
+// times the direction.
+//
+// Taps: with use_tex the 4 x 4 window comes from four tex2Dgather fetches of the coefficient
+// image held in a CUDA array (block-linear, so rays in every direction stay cache-friendly);
+// each fetch is centred on an integer texel corner, so it returns four stored values exactly
+// (no filtering).  Otherwise the taps are plain global loads from the padded coefficient image.
+
+// Shared-memory layout of a forward row CTA (float2 units): bufA, bufB (nc each), the 16-byte
+// aligned anchor table (float4 per sub-angle and tile), the sub-angle directions, the twiddles.
+__host__ __device__ __forceinline__ int fwd_anchor_offset(const DevPlan& p) { return (2 * p.nc + 1) & ~1; }
+__host__ __device__ __forceinline__ int fwd_tw_offset(const DevPlan& p) {
+  return fwd_anchor_offset(p) + 2 * p.r * p.n_eanc + p.r + 1;
+}
+
+// Interpolant from the texture at unpadded index coordinates (ic + ac, ir + ar).
+__device__ __forceinline__ float sample_image_tex(cudaTextureObject_t tex, int ic, float ac, int ir, float ar, bool cubic) {
+  if (cubic) {
+    float wc[4], wr[4];
+    bspline_w(ac, wc);
+    bspline_w(ar, wr);
+    // gather at (x0 + 1, y0 + 1) returns texels (x0, y1), (x0+1, y1), (x0+1, y0), (x0, y0) in .x .y .z .w
+    const float x0 = static_cast<float>(ic - 1) + 1.f, x1 = x0 + 2.f;
+    const float y0 = static_cast<float>(ir - 1) + 1.f, y1 = y0 + 2.f;
+    const float4 g00 = tex2Dgather<float4>(tex, x0, y0, 0);  // rows ir-1, ir   cols ic-1, ic
+    const float4 g10 = tex2Dgather<float4>(tex, x1, y0, 0);  // rows ir-1, ir   cols ic+1, ic+2
+    const float4 g01 = tex2Dgather<float4>(tex, x0, y1, 0);  // rows ir+1, ir+2 cols ic-1, ic
+    const float4 g11 = tex2Dgather<float4>(tex, x1, y1, 0);  // rows ir+1, ir+2 cols ic+1, ic+2
+    const float r0 = fmaf(wc[0], g00.w, fmaf(wc[1], g00.z, fmaf(wc[2], g10.w, wc[3] * g10.z)));
+    const float r1 = fmaf(wc[0], g00.x, fmaf(wc[1], g00.y, fmaf(wc[2], g10.x, wc[3] * g10.y)));
+    const float r2 = fmaf(wc[0], g01.w, fmaf(wc[1], g01.z, fmaf(wc[2], g11.w, wc[3] * g11.z)));
+    const float r3 = fmaf(wc[0], g01.x, fmaf(wc[1], g01.y, fmaf(wc[2], g11.x, wc[3] * g11.y)));
+    return fmaf(wr[0], r0, fmaf(wr[1], r1, fmaf(wr[2], r2, wr[3] * r3)));
+  }
+  const float4 g = tex2Dgather<float4>(tex, static_cast<float>(ic) + 1.f, static_cast<float>(ir) + 1.f, 0);
+  const float v0 = fmaf(ac, g.z - g.w, g.w);  // row ir
+  const float v1 = fmaf(ac, g.y - g.x, g.x);  // row ir + 1
+  return fmaf(ar, v1 - v0, v0);
+}
+
+__device__ void sample_row_forward(const DevPlan& p, int m, int jj, float* __restrict__ h, float4* __restrict__ anc,
+                                   float2* __restrict__ dir) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int r = p.r, ne = p.n_eanc;
+  const bool cubic = p.interp == 3;
   const float4 um = p.fwd_m[m];
-  const float4* rowc = p.fwd_row + (static_cast<size_t>(m) * p.nh + jj) * p.r;
-  for (int tile = warp; tile < p.n_eanc; tile += nw) {
+  const float4* rowc = p.fwd_row + (static_cast<size_t>(m) * p.nh + jj) * r;
+  for (int idx = threadIdx.x; idx < r * ne; idx += blockDim.x) {
+    const int q = idx / ne, tile = idx - q * ne;
+    const float4 cs = rowc[q];
+    const float2 ea = p.fwd_eanc[tile];
+    float ch, cl, rh, rl;
+    df_mul_add(ea.x, ea.y, cs.x, cs.y, um.x, um.y, &ch, &cl);
+    df_mul_add(ea.x, ea.y, cs.z, cs.w, um.z, um.w, &rh, &rl);
+    const float Ic = floorf(ch), Ir = floorf(rh);
+    anc[idx] = make_float4(Ic, (ch - Ic) + cl, Ir, (rh - Ir) + rl);
+    if (tile == 0) dir[q] = make_float2(cs.x, cs.z);
+  }
+  __syncthreads();
+  const int P = p.img_pitch;
+  for (int tile = warp; tile < ne; tile += nw) {
     const int i = tile * kETile + lane;
     const bool valid = i < p.N_rho;
     const float2 e = valid ? p.fwd_e[i] : make_float2(0.f, 0.f);
-    const float2 ea = p.fwd_eanc[tile];
     float acc = 0.f;
-    for (int q = 0; q < p.r; ++q) {
-      const float4 cs = rowc[q];
-      float ch, cl, rh, rl;
-      df_mul_add(ea.x, ea.y, cs.x, cs.y, um.x, um.y, &ch, &cl);
-      df_mul_add(ea.x, ea.y, cs.z, cs.w, um.z, um.w, &rh, &rl);
-      const float Ic = floorf(ch), Ir = floorf(rh);
-      const float Fc = fmaf(e.y, cs.x, (ch - Ic) + cl);
-      const float Fr = fmaf(e.y, cs.z, (rh - Ir) + rl);
+    for (int q = 0; q < r; ++q) {
+      const float4 a = anc[q * ne + tile];
+      const float2 d = dir[q];
+      const float Fc = fmaf(e.y, d.x, a.y);
+      const float Fr = fmaf(e.y, d.y, a.w);
       const float fc = floorf(Fc), fr = floorf(Fr);
-      acc += sample_image(p, static_cast<int>(Ic) + static_cast<int>(fc), Fc - fc, static_cast<int>(Ir) + static_cast<int>(fr),
-                          Fr - fr);
+      const int ic = static_cast<int>(a.x + fc), ir = static_cast<int>(a.z + fr);  // padded indices
+      if (ic < 1 || ic > P - 3 || ir < 1 || ir > P - 3) continue;                 // every tap is zero
+      acc += p.use_tex ? sample_image_tex(p.tex_img, ic - kPad, Fc - fc, ir - kPad, Fr - fr, cubic)
+                       : sample_image(p, ic, Fc - fc, ir, Fr - fr);
     }
     if (valid) h[i] = acc * e.x;
   }
 }
 
-// Value of the sinogram interpolant at (theta index It + at, padded s index is + as).
-__device__ __forceinline__ float sample_sino(const DevPlan& p, int It, float at, int is, float as) {
-  const int na = p.n_angles, pitch = p.sino_pitch;
-  const int ntap = p.interp == 3 ? 4 : 2;
-  float wt[4], ws[4];
-  if (p.interp == 3) {
-    bspline_w(at, wt);
-    bspline_w(as, ws);
-    It -= 1;
-    is -= 1;
-  } else {
-    wt[0] = 1.f - at;
-    wt[1] = at;
-    ws[0] = 1.f - as;
-    ws[1] = as;
-  }
-  float acc = 0.f;
-  for (int dt = 0; dt < ntap; ++dt) {
-    int a2 = (It + dt) % (2 * na);
-    if (a2 < 0) a2 += 2 * na;
-    const bool flip = a2 >= na;
-    const float* row = p.coef_sino + static_cast<size_t>(flip ? a2 - na : a2) * pitch;
-    float v = 0.f;
-    for (int ds = 0; ds < ntap; ++ds) {
-      int c = is + ds;
-      if (flip) c = p.n_det + 2 * kPad - c;
-      c = clampi(c, 0, pitch - 1);
-      v = fmaf(ws[ds], __ldg(row + c), v);
-    }
-    acc = fmaf(wt[dt], v, acc);
-  }
-  return acc;
-}
-
 // Back-projection: G(phi_j, rho_i) = g~(phi_j + m beta, (e^rho_i - (1 - a_R) cos phi_j) / a_R).
+// The theta taps (rows of the extended sinogram, flips, weights) are the same for the whole row;
+// a flipped row (theta + pi) is read at k -> n_det - k, i.e. with reversed s weights.
 __device__ void sample_row_backproject(const DevPlan& p, int m, int jj, float* __restrict__ h) {
   const int2 th = p.bp_th[m * p.nh + jj];
   const int2 cj = p.bp_c[jj];
   const float Ft = __int_as_float(th.y), Fc = __int_as_float(cj.y);
+  const int na = p.n_angles, pitch = p.sino_pitch;
+  const int K = p.n_det + 2 * kPad;  // padded index of a flipped tap: K - c
+  const bool cubic = p.interp == 3;
+  const int ntap = cubic ? 4 : 2;
+  float wt[4];
+  const float* rows[4];
+  bool flip[4];
+  if (cubic) {
+    bspline_w(Ft, wt);
+  } else {
+    wt[0] = 1.f - Ft;
+    wt[1] = Ft;
+    wt[2] = wt[3] = 0.f;
+  }
+  const int t0 = cubic ? th.x - 1 : th.x;
+  for (int dt = 0; dt < 4; ++dt) {
+    int a2 = (t0 + dt) % (2 * na);
+    if (a2 < 0) a2 += 2 * na;
+    flip[dt] = a2 >= na;
+    rows[dt] = p.coef_sino + static_cast<size_t>(flip[dt] ? a2 - na : a2) * pitch;
+  }
   for (int i = threadIdx.x; i < p.N_rho; i += blockDim.x) {
     const int2 ei = p.bp_e[i];
     const float F = __int_as_float(ei.y) + Fc;
     const float fl = floorf(F);
-    h[i] = sample_sino(p, th.x, Ft, ei.x + cj.x + static_cast<int>(fl), F - fl);
+    const int is = ei.x + cj.x + static_cast<int>(fl);
+    const float as = F - fl;
+    float acc = 0.f;
+    if (cubic) {
+      float ws[4];
+      bspline_w(as, ws);
+      const int bf = clampi(is - 1, 0, pitch - 4);       // forward taps is-1 .. is+2
+      const int bb = clampi(K - is - 2, 0, pitch - 4);   // flipped taps K-is-2 .. K-is+1
+#pragma unroll
+      for (int dt = 0; dt < 4; ++dt) {
+        const float* r = rows[dt] + (flip[dt] ? bb : bf);
+        const float x0 = __ldg(r), x1 = __ldg(r + 1), x2 = __ldg(r + 2), x3 = __ldg(r + 3);
+        const float v = flip[dt] ? fmaf(ws[3], x0, fmaf(ws[2], x1, fmaf(ws[1], x2, ws[0] * x3)))
+                                 : fmaf(ws[0], x0, fmaf(ws[1], x1, fmaf(ws[2], x2, ws[3] * x3)));
+        acc = fmaf(wt[dt], v, acc);
+      }
+    } else {
+      const int bf = clampi(is, 0, pitch - 2);
+      const int bb = clampi(K - is - 1, 0, pitch - 2);
+      for (int dt = 0; dt < ntap; ++dt) {
+        const float* r = rows[dt] + (flip[dt] ? bb : bf);
+        const float x0 = __ldg(r), x1 = __ldg(r + 1);
+        const float v = flip[dt] ? fmaf(as, x0 - x1, x1) : fmaf(as, x1 - x0, x0);
+        acc = fmaf(wt[dt], v, acc);
+      }
+    }
+    h[i] = acc;
   }
 }
 
 // Sample one angular row, real FFT along rho, write the half spectrum (N_rho/2 + 1 bins).
 template <bool BACK>
 __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   const int nc = p.nc;
   float2* bufA = smem;
   float2* bufB = smem + nc;
+  const float2* tw;
   const int jj = blockIdx.x, m = blockIdx.y;
-  if (BACK)
+  if (BACK) {
+    float2* tws = smem + 2 * nc;
+    if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
+    tw = p.rows_tw_smem ? tws : p.tw_rho;
     sample_row_backproject(p, m, jj, reinterpret_cast<float*>(bufA));
-  else
-    sample_row_forward(p, m, jj, reinterpret_cast<float*>(bufA));
+  } else {
+    float4* anc = reinterpret_cast<float4*>(smem + fwd_anchor_offset(p));
+    float2* tws = smem + fwd_tw_offset(p);
+    if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
+    tw = p.rows_tw_smem ? tws : p.tw_rho;
+    sample_row_forward(p, m, jj, reinterpret_cast<float*>(bufA), anc, reinterpret_cast<float2*>(anc + p.r * p.n_eanc));
+  }
   __syncthreads();
-  const float2* Z = fft_block<false>(bufA, bufB, 1, nc, p.rad_rho, p.tw_rho, threadIdx.x, blockDim.x);
+  const float2* Z = fft_block<false>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
   float2* out = p.xspec + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch;
   for (int k = threadIdx.x; k <= nc; k += blockDim.x) {
     const float2 zk = Z[k == nc ? 0 : k];
@@ -324,11 +412,13 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
 // FFT along theta of col_group rho frequencies, multiply by the kernel, inverse FFT, keep the
 // centre half plus the halo rows.
 __global__ void __launch_bounds__(kThreads) k_columns(DevPlan p, const float2* __restrict__ kern) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   const int nt = p.n_theta, nh = p.nh, nc = p.nc;
   const int G = p.col_group;
   float2* A = smem;
   float2* B = smem + G * nt;
+  float2* tw = smem + 2 * G * nt;
+  stage_table(tw, p.tw_th, nt, threadIdx.x, blockDim.x);
   const int m = blockIdx.y, kr0 = blockIdx.x * G;
   const float2* xin = p.xspec + static_cast<size_t>(m) * nh * p.x_pitch;
   for (int idx = threadIdx.x; idx < G * nt; idx += blockDim.x) {
@@ -339,7 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_columns(DevPlan p, const float2* _
     A[g * nt + j] = v;
   }
   __syncthreads();
-  float2* S = fft_block<false>(A, B, G, nt, p.rad_th, p.tw_th, threadIdx.x, blockDim.x);
+  float2* S = fft_block<false>(A, B, G, nt, p.rad_th, tw, threadIdx.x, blockDim.x);
   float2* T = (S == A) ? B : A;
   const int nkt = nt / 2 + 1;
   for (int idx = threadIdx.x; idx < G * nt; idx += blockDim.x) {
@@ -351,7 +441,7 @@ __global__ void __launch_bounds__(kThreads) k_columns(DevPlan p, const float2* _
     }
   }
   __syncthreads();
-  const float2* Y = fft_block<true>(S, T, G, nt, p.rad_th, p.tw_th, threadIdx.x, blockDim.x);
+  const float2* Y = fft_block<true>(S, T, G, nt, p.rad_th, tw, threadIdx.x, blockDim.x);
   float2* yout = p.yspec + static_cast<size_t>(m) * (nh + kHaloLo + kHaloHi) * p.x_pitch;
   const int nrow = nh + kHaloLo + kHaloHi;
   for (int idx = threadIdx.x; idx < G * nrow; idx += blockDim.x) {
@@ -363,10 +453,13 @@ __global__ void __launch_bounds__(kThreads) k_columns(DevPlan p, const float2* _
 
 // Inverse real FFT along rho of one kept row; writes N_rho values plus kPad wrap columns per side.
 __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   const int nc = p.nc, nr = p.N_rho;
   float2* bufA = smem;
   float2* bufB = smem + nc;
+  float2* tws = smem + 2 * nc;
+  if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
+  const float2* tw = p.rows_tw_smem ? tws : p.tw_rho;
   const int row = blockIdx.x, m = blockIdx.y;
   const int nrow = p.nh + kHaloLo + kHaloHi;
   const float2* X = p.yspec + (static_cast<size_t>(m) * nrow + row) * p.x_pitch;
@@ -378,7 +471,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
     bufA[k] = make_float2(sm.x - df.y, sm.y + df.x);      // + i * df
   }
   __syncthreads();
-  const float2* Z = fft_block<true>(bufA, bufB, 1, nc, p.rad_rho, p.tw_rho, threadIdx.x, blockDim.x);
+  const float2* Z = fft_block<true>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
   const float* h = reinterpret_cast<const float*>(Z);
   float* y = p.ylp + (static_cast<size_t>(m) * nrow + row) * p.y_pitch;
   for (int c = static_cast<int>(threadIdx.x) - kPad; c < nr + kPad; c += blockDim.x) {
@@ -426,7 +519,7 @@ __global__ void __launch_bounds__(128) k_gather_sino(DevPlan p, float* __restric
   const int nd = p.n_det;
   if (k >= nd) return;
   float out = 0.f;
-  if (live_bin(k, nd)) {
+  if (k >= p.live_lo && k <= p.live_hi) {
     const int4 ang = p.fwd_ang[a];
     const int4 anc = p.fwd_anc[static_cast<size_t>(a) * p.n_ktiles + k / kKTile];
     const int n = k - (k / kKTile) * kKTile;
@@ -469,8 +562,13 @@ __global__ void __launch_bounds__(kPTile * kPTile) k_gather_image(DevPlan p, flo
   img[static_cast<size_t>(i) * N + j] = acc;
 }
 
-size_t rows_smem(const DevPlan& p) { return 2 * static_cast<size_t>(p.nc) * sizeof(float2); }
-size_t cols_smem(const DevPlan& p) { return 2 * static_cast<size_t>(p.col_group) * p.n_theta * sizeof(float2); }
+size_t rows_smem(const DevPlan& p) {
+  return (2 + (p.rows_tw_smem ? 1 : 0)) * static_cast<size_t>(p.nc) * sizeof(float2);
+}
+size_t rows_fwd_smem(const DevPlan& p) {
+  return (static_cast<size_t>(fwd_tw_offset(p)) + (p.rows_tw_smem ? p.nc : 0)) * sizeof(float2);
+}
+size_t cols_smem(const DevPlan& p) { return (2 * static_cast<size_t>(p.col_group) + 1) * p.n_theta * sizeof(float2); }
 
 void launch_columns_and_inverse(const DevPlan& p, const float2* kern, cudaStream_t st, const StageHook& hook,
                                 int stage0) {
@@ -483,14 +581,18 @@ void launch_columns_and_inverse(const DevPlan& p, const float2* kern, cudaStream
 
 }  // namespace
 
-cudaError_t configure_kernels(const DevPlan& p) {
+cudaError_t configure_kernels(DevPlan& p) {
   // The limit is a per-function attribute shared by every plan on the device: raise it to the
   // device's opt-in maximum (never to one plan's need, which a later, smaller plan would lower).
   cudaError_t e;
   int dev = 0, optin = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-  if (rows_smem(p) > static_cast<size_t>(optin) || cols_smem(p) > static_cast<size_t>(optin)) return cudaErrorInvalidValue;
+  p.rows_tw_smem = 1;  // stage the rho twiddles in shared memory when everything fits
+  if (rows_fwd_smem(p) > static_cast<size_t>(optin) || rows_smem(p) > static_cast<size_t>(optin)) p.rows_tw_smem = 0;
+  if (rows_fwd_smem(p) > static_cast<size_t>(optin) || rows_smem(p) > static_cast<size_t>(optin) ||
+      cols_smem(p) > static_cast<size_t>(optin))
+    return cudaErrorInvalidValue;
   const int rs = optin, cs = optin;
   if ((e = cudaFuncSetAttribute(k_rows_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_rows_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
@@ -500,11 +602,12 @@ cudaError_t configure_kernels(const DevPlan& p) {
 }
 
 cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cudaStream_t st, StageHook hook) {
-  const int tiles = (p.N + kPfTile - 1) / kPfTile;
   hook(-1, st);
-  k_prefilter_image<<<dim3(tiles, tiles), kThreads, 0, st>>>(p, image);
+  ImageSource isrc{image, p.N};
+  k_prefilter<ImageSource><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows), kThreads, 0, st>>>(
+      p, isrc, p.N, p.N, p.coef_img, p.img_pitch, kPad, p.use_tex ? p.surf_img : 0);
   hook(0, st);
-  k_rows_fwd<false><<<dim3(p.nh, p.M), kThreads, rows_smem(p), st>>>(p);
+  k_rows_fwd<false><<<dim3(p.nh, p.M), kThreads, rows_fwd_smem(p), st>>>(p);
   hook(1, st);
   launch_columns_and_inverse(p, p.k_fwd, st, hook, 2);
   k_gather_sino<<<dim3((p.n_det + 127) / 128, p.n_angles), 128, 0, st>>>(p, sino);
@@ -514,8 +617,9 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
 
 cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook) {
   hook(-1, st);
-  k_prefilter_sino<<<dim3((p.n_det + 1 + kPfTile - 1) / kPfTile, (p.n_angles + kPfTile - 1) / kPfTile), kThreads, 0, st>>>(
-      p, sino);
+  SinoSource ssrc{sino, p.n_angles, p.n_det, p.live_lo, p.live_hi};
+  k_prefilter<SinoSource><<<dim3((p.n_det + 1 + kPfCols - 1) / kPfCols, (p.n_angles + kPfRows - 1) / kPfRows), kThreads, 0,
+                            st>>>(p, ssrc, p.n_angles, p.n_det + 1, p.coef_sino, p.sino_pitch, 0, 0);
   hook(5, st);
   k_rows_fwd<true><<<dim3(p.nh, p.M), kThreads, rows_smem(p), st>>>(p);
   hook(6, st);

@@ -19,6 +19,7 @@ struct DevPlan {
   int y_pitch;     // real log-polar rows with periodic wrap columns: >= N_rho + 2 kPad
   int n_eanc, n_ktiles, n_ptiles;
   int col_group;   // rho frequencies per column CTA (4, 2 or 1: shared memory bound)
+  int live_lo, live_hi;  // detector bins with |s| < 1 are exactly [live_lo, live_hi]
   float inv_drho, inv_dphi, inv_aR, d_s;
   RadixList rad_rho, rad_th;
   // tables
@@ -42,6 +43,10 @@ struct DevPlan {
   const float* filt;   // FBP transfer function (n_filt_c complex bins) or null
   // scratch
   float* coef_img;     // (N + 2 kPad)^2, zero border
+  int use_tex;         // 1: the forward sampling reads the coefficient image through tex_img
+  cudaTextureObject_t tex_img;   // N x N CUDA array holding Q f (border mode: zero outside)
+  cudaSurfaceObject_t surf_img;  // write view of the same array (filled by the pre-filter)
+  int rows_tw_smem;    // 1: row kernels stage the rho twiddles in shared memory
   float* coef_sino;    // n_angles x sino_pitch, zero border
   float2* xspec;       // M x nh x x_pitch
   float2* yspec;       // M x (nh + 4) x x_pitch
@@ -69,6 +74,6 @@ cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image
 cudaError_t launch_sino_filter(const DevPlan& p, const float* sino, float* out, cudaStream_t st);
 
 // Dynamic shared memory limits are raised once per device.
-cudaError_t configure_kernels(const DevPlan& p);
+cudaError_t configure_kernels(DevPlan& p);
 
 }  // namespace radon
