@@ -63,6 +63,7 @@ typedef struct {
   int n_theta;        /* angular FFT length, 2 * n_theta_half, period [-beta, beta)           */
   int r;              /* fine angular sub-samples per coarse angle (Omega_lp -> Omega_p)       */
   int n_quad;         /* trapezoid nodes used for the kernel integrals (Eq. weightsa)          */
+  int n_filter;       /* zero-padded FFT length of the FBP filter along s (>= 2 n_det)          */
   double beta, a_R, a_r, L;       /* pi/M, Eq. aconst, L = -log(a_r)                           */
   double d_phi, d_rho, d_s, d_theta;
   size_t device_bytes;            /* device memory owned by the plan (tables + scratch)        */
@@ -88,9 +89,15 @@ int radon_forward(radon_plan plan, const float* d_image, float* d_sino, void* st
 /* R#: d_sino [n_angles][n_det] -> d_image [N][N] (overwritten).  Algorithm 2. */
 int radon_backproject(radon_plan plan, const float* d_sino, float* d_image, void* stream);
 
-/* Filtered back-projection f = R# W g (Eq. FBP): W filters each sinogram row along s with the
- * transfer function selected by `filter` (band-limited to |sigma| <= sigma_max = 1/(2 ds)),
- * then R# is applied.  d_sino is not modified. */
+/* Filtered back-projection f = R# W g (Eq. FBP), with R# over [0, pi) so that f = R# W R f for
+ * W = |sigma| (sigma in cycles per unit of s).  W acts on each sinogram row (bins with |s| >= 1
+ * taken as zero) as a discrete convolution along s, evaluated with a zero-padded FFT of length
+ * n_filter.  Its transfer function is ds times the DFT of the band-limited ramp kernel
+ * h(0) = 1/(4 ds^2), h(n) = -1/(pi^2 n^2 ds^2) for odd n, 0 for even n != 0 (Eq. ramp, with the
+ * low-frequency behaviour of the sampled kernel instead of a kink at sigma = 0), times the
+ * window of `filter`: 1 (ramp), sinc(sigma / (2 sigma_max)) (Shepp-Logan, Eq. SLfilt) or
+ * cos(pi sigma / (2 sigma_max)) (cosine, Eq. cosfilt), sigma_max = 1/(2 ds).  Then R# is applied.
+ * d_sino is not modified; the filtered sinogram lives in plan-owned memory. */
 int radon_fbp(radon_plan plan, const float* d_sino, float* d_image, int filter, void* stream);
 
 /* Same as radon_forward / radon_backproject but with HOST buffers: the call copies the input to
@@ -117,8 +124,8 @@ int radon_kernel_quadrant(int N, int n_angles, int n_det, int n_partitions, int 
  * Stages: 0 image pre-filter, 1 forward row sampling + rho FFT, 2 forward theta convolution,
  * 3 forward inverse rho FFT, 4 sinogram gather, 5 sinogram pre-filter, 6 back-projection row
  * sampling + rho FFT, 7 back-projection theta convolution, 8 back-projection inverse rho FFT,
- * 9 image gather. */
-#define RADON_NUM_STAGES 10
+ * 9 image gather, 10 FBP filter along s. */
+#define RADON_NUM_STAGES 11
 int radon_profile_enable(radon_plan plan, int enable);
 int radon_profile_read(radon_plan plan, double* ms, int* launches);
 

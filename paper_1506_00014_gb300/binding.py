@@ -22,7 +22,7 @@ class radon_plan_info(ctypes.Structure):
     _fields_ = [
         ("N", _c_int), ("n_angles", _c_int), ("n_det", _c_int), ("interp_order", _c_int),
         ("n_partitions", _c_int), ("N_rho", _c_int), ("n_theta_half", _c_int), ("n_theta", _c_int),
-        ("r", _c_int), ("n_quad", _c_int),
+        ("r", _c_int), ("n_quad", _c_int), ("n_filter", _c_int),
         ("beta", ctypes.c_double), ("a_R", ctypes.c_double), ("a_r", ctypes.c_double), ("L", ctypes.c_double),
         ("d_phi", ctypes.c_double), ("d_rho", ctypes.c_double), ("d_s", ctypes.c_double),
         ("d_theta", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
@@ -41,10 +41,10 @@ EXPORTED = (
     "radon_profile_read", "radon_forward_static_scratch",
 )
 
-RADON_NUM_STAGES = 10
+RADON_NUM_STAGES = 11
 STAGE_NAMES = (
     "prefilter_image", "rows_fwd", "columns_fwd", "rows_inv_fwd", "gather_sino",
-    "prefilter_sino", "rows_bp", "columns_bp", "rows_inv_bp", "gather_image",
+    "prefilter_sino", "rows_bp", "columns_bp", "rows_inv_bp", "gather_image", "sino_filter",
 )
 
 _lib = None

@@ -141,6 +141,7 @@ int compute_geometry(int N, int n_angles, int n_det, int interp, int M, radon_pl
   long nq = 64;
   while (nq < need) nq <<= 1;
   g->n_quad = static_cast<int>(nq);
+  g->n_filter = static_cast<int>(even_7smooth_at_least(2L * n_det));
   return RADON_OK;
 }
 
@@ -375,6 +376,36 @@ int build_tables(const radon_plan_info& g, HostTables* t) {
         o[6] = 0;
         o[7] = 0;
       }
+  }
+
+  // FBP transfer functions on the n_filter-point DFT grid (sigma_k = k / (n_filter ds)):
+  // ds * DFT of the band-limited ramp kernel, times the window, divided by n_filter (the inverse
+  // real FFT on the device is unnormalised).
+  {
+    const int P = g.n_filter, nf = P / 2;
+    if (!factor_radices(nf, &t->rad_filt)) return RADON_NOT_SUPPORTED;
+    twiddles(nf, nf, &t->tw_filt);
+    twiddles(P, nf + 1, &t->tw_filt_r2c);
+    const double ds = g.d_s;
+    std::vector<double> h(nf + 1, 0.0);  // h(n), n = 0..P/2 (even kernel, h(-P/2) = h(P/2))
+    h[0] = 1.0 / (4.0 * ds * ds);
+    for (int n = 1; n <= nf; n += 2) h[n] = -1.0 / (kPi * kPi * static_cast<double>(n) * n * ds * ds);
+    t->filt.assign(3 * static_cast<size_t>(nf + 1), 0.f);
+    std::vector<double> H(nf + 1);
+    parallel_for(nf + 1, [&](int b, int e) {
+      for (int k = b; k < e; ++k) {
+        double acc = h[0] + h[nf] * ((k & 1) ? -1.0 : 1.0);
+        for (int n = 1; n < nf; n += 2) acc += 2.0 * h[n] * std::cos(2.0 * kPi * static_cast<double>(k) * n / P);
+        H[k] = ds * acc;
+      }
+    });
+    for (int k = 0; k <= nf; ++k) {
+      const double x = kPi * k / P;  // pi sigma_k / (2 sigma_max)
+      const double sl = k == 0 ? 1.0 : std::sin(x) / x;
+      t->filt[k] = static_cast<float>(H[k] / P);
+      t->filt[(nf + 1) + k] = static_cast<float>(H[k] * sl / P);
+      t->filt[2 * (nf + 1) + k] = static_cast<float>(H[k] * std::cos(x) / P);
+    }
   }
 
   // Truncated pre-filter: (Q f)_k = sum_n sqrt(3) z^|n| f_{k+n}, the impulse response of the

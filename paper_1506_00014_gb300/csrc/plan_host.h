@@ -61,6 +61,11 @@ struct HostTables {
   std::vector<int32_t> bp_anc;   // 8 per (m, tile): I_theta, F_theta, I_rho, F_rho, y0x, y0y, 0, 0
   std::vector<float> bp_m;       // 2 per m: a_R cos(m beta), a_R sin(m beta)
   std::vector<float> fir;        // kFirHalf + 1 pre-filter taps sqrt(3) z^n
+  // FBP filter along s: real FFT of length n_filter (complex length n_filter / 2)
+  Radices rad_filt;
+  std::vector<float> tw_filt;     // 2 * (n_filter/2): exp(-2 pi i p / (n_filter/2))
+  std::vector<float> tw_filt_r2c; // 2 * (n_filter/2 + 1): exp(-2 pi i k / n_filter)
+  std::vector<float> filt;        // 3 * (n_filter/2 + 1): transfer functions / n_filter (ramp, SL, cosine)
 };
 
 int build_tables(const radon_plan_info& g, HostTables* t);

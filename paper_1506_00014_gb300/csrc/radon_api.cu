@@ -100,6 +100,27 @@ radon::StageHook hook_of(radon_plan_s* p) {
   return h;
 }
 
+// A width x height float CUDA array with a point-sampled, zero-border texture and a surface.
+cudaError_t make_texture(int width, int height, cudaArray_t* arr, cudaTextureObject_t* tex, cudaSurfaceObject_t* surf) {
+  cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
+  cudaError_t e = cudaMallocArray(arr, &fd, width, height, cudaArraySurfaceLoadStore);
+  if (e != cudaSuccess) return e;
+  cudaResourceDesc rd;
+  std::memset(&rd, 0, sizeof(rd));
+  rd.resType = cudaResourceTypeArray;
+  rd.res.array.array = *arr;
+  cudaTextureDesc td;
+  std::memset(&td, 0, sizeof(td));
+  td.addressMode[0] = cudaAddressModeBorder;
+  td.addressMode[1] = cudaAddressModeBorder;
+  td.filterMode = cudaFilterModePoint;
+  td.readMode = cudaReadModeElementType;
+  td.normalizedCoords = 0;
+  e = cudaCreateTextureObject(tex, &rd, &td, nullptr);
+  if (e == cudaSuccess) e = cudaCreateSurfaceObject(surf, &rd);
+  return e;
+}
+
 bool on_plan_device(const radon_plan_s* p) {
   int dev = -1;
   return cudaGetDevice(&dev) == cudaSuccess && dev == p->device;
@@ -145,6 +166,9 @@ void radon_plan_destroy(radon_plan plan) {
   if (plan->dp.tex_img) cudaDestroyTextureObject(plan->dp.tex_img);
   if (plan->dp.surf_img) cudaDestroySurfaceObject(plan->dp.surf_img);
   if (plan->img_array) cudaFreeArray(plan->img_array);
+  if (plan->dp.tex_lp) cudaDestroyTextureObject(plan->dp.tex_lp);
+  if (plan->dp.surf_lp) cudaDestroySurfaceObject(plan->dp.surf_lp);
+  if (plan->lp_array) cudaFreeArray(plan->lp_array);
   cudaFree(plan->table_mem);
   cudaFree(plan->scratch_mem);
   delete plan;
@@ -207,7 +231,9 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.inv_dphi = static_cast<float>(1.0 / g.d_phi);
   d.inv_aR = static_cast<float>(1.0 / g.a_R);
   d.d_s = static_cast<float>(g.d_s);
-  if (!copy_radices(t.rad_rho, 1, &d.rad_rho) || !copy_radices(t.rad_th, d.col_group, &d.rad_th)) {
+  d.n_filt = g.n_filter;
+  if (!copy_radices(t.rad_rho, 1, &d.rad_rho) || !copy_radices(t.rad_th, d.col_group, &d.rad_th) ||
+      !copy_radices(t.rad_filt, 1, &d.rad_filt)) {
     delete p;
     return RADON_NOT_SUPPORTED;
   }
@@ -219,6 +245,7 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   const size_t o_fang = tp.add(t.fwd_ang), o_fanc = tp.add(t.fwd_anc);
   const size_t o_bth = tp.add(t.bp_th), o_bc = tp.add(t.bp_c), o_be = tp.add(t.bp_e);
   const size_t o_banc = tp.add(t.bp_anc), o_bm = tp.add(t.bp_m), o_fir = tp.add(t.fir);
+  const size_t o_twf = tp.add(t.tw_filt), o_twfr = tp.add(t.tw_filt_r2c), o_filt = tp.add(t.filt);
 
   const size_t nrow = static_cast<size_t>(d.nh) + radon::kHaloLo + radon::kHaloHi;
   size_t sc = 0;
@@ -232,6 +259,7 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   const size_t s_x = take(sizeof(float2) * static_cast<size_t>(d.M) * d.nh * d.x_pitch);
   const size_t s_ys = take(sizeof(float2) * static_cast<size_t>(d.M) * nrow * d.x_pitch);
   const size_t s_y = take(sizeof(float) * static_cast<size_t>(d.M) * nrow * d.y_pitch);
+  const size_t s_ftmp = take(sizeof(float) * static_cast<size_t>(n_angles) * n_det);
   const size_t s_io_img = take(sizeof(float) * static_cast<size_t>(N) * N);
   const size_t s_io_sino = take(sizeof(float) * static_cast<size_t>(n_angles) * n_det);
 
@@ -263,6 +291,10 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.bp_anc = reinterpret_cast<const int4*>(tb + o_banc);
   d.bp_m = reinterpret_cast<const float2*>(tb + o_bm);
   d.fir = reinterpret_cast<const float*>(tb + o_fir);
+  d.tw_filt = reinterpret_cast<const float2*>(tb + o_twf);
+  d.tw_filt_r2c = reinterpret_cast<const float2*>(tb + o_twfr);
+  d.filt = reinterpret_cast<const float*>(tb + o_filt);
+  d.sino_tmp = reinterpret_cast<float*>(sb + s_ftmp);
   d.coef_img = reinterpret_cast<float*>(sb + s_img);
   d.coef_sino = reinterpret_cast<float*>(sb + s_sino);
   d.xspec = reinterpret_cast<float2*>(sb + s_x);
@@ -272,31 +304,19 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   p->io_sino = reinterpret_cast<float*>(sb + s_io_sino);
   p->info.device_bytes = tp.total() + sc;
 
-  // Coefficient image as a texture over a CUDA array (forward sampling reads it with
-  // tex2Dgather); the pre-filter writes it through a surface.
+  // The coefficient image and the log-polar coefficients also live in CUDA arrays, read with
+  // tex2Dgather (border mode: zero outside) and written through surfaces.
   {
-    cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
-    e = cudaMallocArray(&p->img_array, &fd, N, N, cudaArraySurfaceLoadStore);
-    cudaResourceDesc rd;
-    std::memset(&rd, 0, sizeof(rd));
-    rd.resType = cudaResourceTypeArray;
-    rd.res.array.array = p->img_array;
-    cudaTextureDesc td;
-    std::memset(&td, 0, sizeof(td));
-    td.addressMode[0] = cudaAddressModeBorder;
-    td.addressMode[1] = cudaAddressModeBorder;
-    td.filterMode = cudaFilterModePoint;
-    td.readMode = cudaReadModeElementType;
-    td.normalizedCoords = 0;
-    if (e == cudaSuccess) e = cudaCreateTextureObject(&d.tex_img, &rd, &td, nullptr);
-    if (e == cudaSuccess) e = cudaCreateSurfaceObject(&d.surf_img, &rd);
+    const int lp_rows = static_cast<int>(d.M * nrow);
+    e = make_texture(N, N, &p->img_array, &d.tex_img, &d.surf_img);
+    if (e == cudaSuccess) e = make_texture(d.y_pitch, lp_rows, &p->lp_array, &d.tex_lp, &d.surf_lp);
     if (e != cudaSuccess) {
       cudaGetLastError();
       radon_plan_destroy(p);
       return status_of(e);
     }
     d.use_tex = 1;
-    p->info.device_bytes += sizeof(float) * static_cast<size_t>(N) * N;
+    p->info.device_bytes += sizeof(float) * (static_cast<size_t>(N) * N + static_cast<size_t>(d.y_pitch) * lp_rows);
   }
   e = radon::configure_kernels(d);
   if (e != cudaSuccess) {
@@ -328,8 +348,8 @@ int radon_backproject(radon_plan plan, const float* d_sino, float* d_image, void
 int radon_fbp(radon_plan plan, const float* d_sino, float* d_image, int filter, void* stream) {
   if (!plan || !d_sino || !d_image) return RADON_INVALID_ARG;
   if (filter < RADON_FILTER_RAMP || filter > RADON_FILTER_COSINE) return RADON_INVALID_ARG;
-  (void)stream;
-  return RADON_NOT_SUPPORTED;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  return status_of(radon::launch_fbp(plan->dp, d_sino, d_image, filter, static_cast<cudaStream_t>(stream), hook_of(plan)));
 }
 
 int radon_forward_host(radon_plan plan, const float* h_image, float* h_sino, void* stream) {

@@ -76,6 +76,23 @@ __device__ __forceinline__ void df_mul_add(float ah, float al, float bh, float b
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// atan(y/x) for x > 0 and |y/x| < 0.1 by its Maclaurin series x - x^3/3 + x^5/5 (remainder
+// below |y/x|^7 / 7 < 1.5e-8); other arguments use atan2f.
+__device__ __forceinline__ float small_atan2(float y, float x) {
+  const float t = y / x;
+  if (!(x > 0.f) || fabsf(t) >= 0.1f) return atan2f(y, x);
+  const float t2 = t * t;
+  return t * fmaf(t2, fmaf(t2, 0.2f, -1.f / 3.f), 1.f);
+}
+
+// log(1 + u) for |u| < 0.1 by its Maclaurin series up to u^7 (remainder below |u|^8 / 8 <
+// 1.3e-9); other arguments use log1pf.
+__device__ __forceinline__ float small_log1p(float u) {
+  if (fabsf(u) >= 0.1f) return log1pf(u);
+  const float p = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, 1.f / 7.f, -1.f / 6.f), 0.2f), -0.25f), 1.f / 3.f), -0.5f), 1.f);
+  return u * p;
+}
+
 // ------------------------------------------------------------------------------------------
 // Pre-filters.  One CTA computes a kPfRows x kPfCols tile of coefficients from the tile plus a
 // kFirHalf halo, staged in shared memory; the FIR runs along rows and then along columns, each
@@ -138,9 +155,20 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
   const int r0 = blockIdx.y * kPfRows - kFirHalf, c0 = blockIdx.x * kPfCols - kFirHalf;
   const int tid = threadIdx.x;
   if (src.interior(r0, r0 + kPfInR, c0, c0 + kPfInC)) {
-    for (int idx = tid; idx < kPfInR * kPfInC; idx += kThreads) {
+    // all loads of this thread are issued before the first shared-memory store
+    constexpr int kPer = (kPfInR * kPfInC + kThreads - 1) / kThreads;
+    float v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int idx = tid + k * kThreads;
       const int ly = idx / kPfInC, lx = idx - ly * kPfInC;
-      s_in[ly][lx] = src.direct(r0 + ly, c0 + lx);
+      v[k] = idx < kPfInR * kPfInC ? src.direct(r0 + ly, c0 + lx) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int idx = tid + k * kThreads;
+      const int ly = idx / kPfInC, lx = idx - ly * kPfInC;
+      if (idx < kPfInR * kPfInC) s_in[ly][lx] = v[k];
     }
   } else {
     for (int idx = tid; idx < kPfInR * kPfInC; idx += kThreads) {
@@ -155,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
       const int ly = idx / kPfCols, lx = idx - ly * kPfCols;
       if (orow + ly < n_rows && ocol + lx < n_cols) {
         const float v = s_in[ly + kFirHalf][lx + kFirHalf];
-        out[static_cast<size_t>(orow + ly + out_r0) * out_pitch + ocol + lx + kPad] = v;
+        if (out) out[static_cast<size_t>(orow + ly + out_r0) * out_pitch + ocol + lx + kPad] = v;
         if (surf) surf2Dwrite(v, surf, (ocol + lx) * static_cast<int>(sizeof(float)), orow + ly);
       }
     }
@@ -193,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
       for (int n = 1; n <= kFirHalf; ++n) acc = fmaf(q[n], w[t + kFirHalf - n] + w[t + kFirHalf + n], acc);
       const int gr = orow + sy + t;
       if (gr < n_rows && gc < n_cols) {
-        out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = acc;
+        if (out) out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = acc;
         if (surf) surf2Dwrite(acc, surf, gc * static_cast<int>(sizeof(float)), gr);
       }
     }
@@ -474,9 +502,13 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
   const float2* Z = fft_block<true>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
   const float* h = reinterpret_cast<const float*>(Z);
   float* y = p.ylp + (static_cast<size_t>(m) * nrow + row) * p.y_pitch;
+  const int yrow = m * nrow + row;
   for (int c = static_cast<int>(threadIdx.x) - kPad; c < nr + kPad; c += blockDim.x) {
     int src = c < 0 ? c + nr : (c >= nr ? c - nr : c);
-    y[c + kPad] = h[src];
+    if (p.use_tex)
+      surf2Dwrite(h[src], p.surf_lp, (c + kPad) * static_cast<int>(sizeof(float)), yrow);
+    else
+      y[c + kPad] = h[src];
   }
 }
 
@@ -484,9 +516,34 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
 // Output gathers.
 
 // Interpolant of partition m's log-polar coefficients at (halo row It + at, padded column
-// Ir + ar); taps are clamped into the array.
+// Ir + ar); taps are clamped into the array.  With use_tex the coefficients are read with
+// tex2Dgather from the CUDA array (partition m occupies rows [m nrow, (m+1) nrow)).
 __device__ __forceinline__ float sample_lp(const DevPlan& p, int m, int It, float at, int Ir, float ar) {
   const int nrow = p.nh + kHaloLo + kHaloHi;
+  if (p.use_tex) {
+    const cudaTextureObject_t t = p.tex_lp;
+    if (p.interp == 3) {
+      float wt[4], wr[4];
+      bspline_w(at, wt);
+      bspline_w(ar, wr);
+      const float y0 = static_cast<float>(m * nrow + clampi(It - 1, 0, nrow - 4)) + 1.f, y1 = y0 + 2.f;
+      const float x0 = static_cast<float>(clampi(Ir - 1, 0, p.y_pitch - 4)) + 1.f, x1 = x0 + 2.f;
+      const float4 g00 = tex2Dgather<float4>(t, x0, y0, 0);
+      const float4 g10 = tex2Dgather<float4>(t, x1, y0, 0);
+      const float4 g01 = tex2Dgather<float4>(t, x0, y1, 0);
+      const float4 g11 = tex2Dgather<float4>(t, x1, y1, 0);
+      const float r0 = fmaf(wr[0], g00.w, fmaf(wr[1], g00.z, fmaf(wr[2], g10.w, wr[3] * g10.z)));
+      const float r1 = fmaf(wr[0], g00.x, fmaf(wr[1], g00.y, fmaf(wr[2], g10.x, wr[3] * g10.y)));
+      const float r2 = fmaf(wr[0], g01.w, fmaf(wr[1], g01.z, fmaf(wr[2], g11.w, wr[3] * g11.z)));
+      const float r3 = fmaf(wr[0], g01.x, fmaf(wr[1], g01.y, fmaf(wr[2], g11.x, wr[3] * g11.y)));
+      return fmaf(wt[0], r0, fmaf(wt[1], r1, fmaf(wt[2], r2, wt[3] * r3)));
+    }
+    const float4 g = tex2Dgather<float4>(t, static_cast<float>(clampi(Ir, 0, p.y_pitch - 2)) + 1.f,
+                                         static_cast<float>(m * nrow + clampi(It, 0, nrow - 2)) + 1.f, 0);
+    const float v0 = fmaf(ar, g.z - g.w, g.w);
+    const float v1 = fmaf(ar, g.y - g.x, g.x);
+    return fmaf(at, v1 - v0, v0);
+  }
   const float* __restrict__ y = p.ylp + static_cast<size_t>(m) * nrow * p.y_pitch;
   if (p.interp == 3) {
     float wt[4], wr[4];
@@ -551,8 +608,8 @@ __global__ void __launch_bounds__(kPTile * kPTile) k_gather_image(DevPlan p, flo
       const float cross = fmaf(y0x, dy2, -y0y * dy1);
       const float r2 = fmaf(y0x, y0x, y0y * y0y);
       const float ydot = fmaf(y0x, dy1, y0y * dy2);
-      const float dth = atan2f(cross, r2 + ydot);
-      const float drho = 0.5f * log1pf(fmaf(2.f, ydot, fmaf(dy1, dy1, dy2 * dy2)) / r2);
+      const float dth = small_atan2(cross, r2 + ydot);
+      const float drho = 0.5f * small_log1p(fmaf(2.f, ydot, fmaf(dy1, dy1, dy2 * dy2)) / r2);
       const float ct = fmaf(dth, p.inv_dphi, __int_as_float(a0.y));
       const float cr = fmaf(drho, p.inv_drho, __int_as_float(a0.w));
       const float ft = floorf(ct), fr = floorf(cr);
@@ -560,6 +617,61 @@ __global__ void __launch_bounds__(kPTile * kPTile) k_gather_image(DevPlan p, flo
     }
   }
   img[static_cast<size_t>(i) * N + j] = acc;
+}
+
+// FBP: filter one sinogram row along s (Eq. FBP, Eq. ramp / SLfilt / cosfilt).  The row (bins
+// with |s| >= 1 zeroed) is zero-padded to n_filt, transformed with the real FFT, multiplied by
+// the real transfer function H (divided by n_filt) and transformed back; the first n_det values
+// are the filtered row.  Bins k and n - k of the half spectrum are handled by one thread, so the
+// spectrum is processed in place.
+__global__ void __launch_bounds__(kThreads) k_sino_filter(DevPlan p, const float* __restrict__ g,
+                                                          const float* __restrict__ H, float* __restrict__ out) {
+  extern __shared__ __align__(16) float2 smem[];
+  const int nf = p.n_filt / 2, nd = p.n_det, a = blockIdx.x;
+  float2* bufA = smem;
+  float2* bufB = smem + nf;
+  float2* tws = smem + 2 * nf;
+  if (p.filt_tw_smem) stage_table(tws, p.tw_filt, nf, threadIdx.x, blockDim.x);
+  const float2* tw = p.filt_tw_smem ? tws : p.tw_filt;
+  float* row = reinterpret_cast<float*>(bufA);
+  const float* gr = g + static_cast<size_t>(a) * nd;
+  for (int k = threadIdx.x; k < 2 * nf; k += blockDim.x)
+    row[k] = (k >= p.live_lo && k <= p.live_hi) ? __ldg(gr + k) : 0.f;
+  __syncthreads();
+  float2* Z = fft_block<false>(bufA, bufB, 1, nf, p.rad_filt, tw, threadIdx.x, blockDim.x);
+  for (int k = threadIdx.x; k <= nf / 2; k += blockDim.x) {
+    const int km = (nf - k) % nf;  // partner bin (0 pairs with itself, giving bins 0 and nf)
+    const float2 zk = Z[k], zm = Z[km];
+    if (k == 0) {
+      const float x0 = zk.x + zk.y, xn = zk.x - zk.y;  // bins 0 and nf of the real transform
+      const float y0 = x0 * __ldg(H), yn = xn * __ldg(H + nf);
+      Z[0] = make_float2(y0 + yn, y0 - yn);
+      continue;
+    }
+    const float2 wk = p.tw_filt_r2c[k], wm = p.tw_filt_r2c[nf - k];
+    // forward real-FFT post-processing for bins k and nf - k
+    const float2 ck = cconj(zm), cm = cconj(zk);
+    const float2 ek = cscale(cadd(zk, ck), 0.5f), dk = cscale(csub(zk, ck), 0.5f);
+    const float2 em = cscale(cadd(zm, cm), 0.5f), dm = cscale(csub(zm, cm), 0.5f);
+    const float2 xk = cadd(ek, cmul(wk, make_float2(dk.y, -dk.x)));
+    const float2 xm = cadd(em, cmul(wm, make_float2(dm.y, -dm.x)));
+    const float2 yk = cscale(xk, __ldg(H + k)), ym = cscale(xm, __ldg(H + nf - k));
+    // inverse real-FFT pre-processing
+    const float2 sk = cadd(yk, cconj(ym)), fk = cmulc(csub(yk, cconj(ym)), wk);
+    const float2 sm = cadd(ym, cconj(yk)), fm = cmulc(csub(ym, cconj(yk)), wm);
+    Z[k] = make_float2(sk.x - fk.y, sk.y + fk.x);
+    if (km != k) Z[km] = make_float2(sm.x - fm.y, sm.y + fm.x);
+  }
+  __syncthreads();
+  float2* other = (Z == bufA) ? bufB : bufA;
+  const float2* Y = fft_block<true>(Z, other, 1, nf, p.rad_filt, tw, threadIdx.x, blockDim.x);
+  const float* y = reinterpret_cast<const float*>(Y);
+  float* o = out + static_cast<size_t>(a) * nd;
+  for (int k = threadIdx.x; k < nd; k += blockDim.x) o[k] = y[k];
+}
+
+size_t filt_smem(const DevPlan& p) {
+  return (2 + (p.filt_tw_smem ? 1 : 0)) * static_cast<size_t>(p.n_filt / 2) * sizeof(float2);
 }
 
 size_t rows_smem(const DevPlan& p) {
@@ -590,9 +702,12 @@ cudaError_t configure_kernels(DevPlan& p) {
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
   p.rows_tw_smem = 1;  // stage the rho twiddles in shared memory when everything fits
   if (rows_fwd_smem(p) > static_cast<size_t>(optin) || rows_smem(p) > static_cast<size_t>(optin)) p.rows_tw_smem = 0;
+  p.filt_tw_smem = 1;
+  if (filt_smem(p) > static_cast<size_t>(optin)) p.filt_tw_smem = 0;
   if (rows_fwd_smem(p) > static_cast<size_t>(optin) || rows_smem(p) > static_cast<size_t>(optin) ||
-      cols_smem(p) > static_cast<size_t>(optin))
+      cols_smem(p) > static_cast<size_t>(optin) || filt_smem(p) > static_cast<size_t>(optin))
     return cudaErrorInvalidValue;
+  if ((e = cudaFuncSetAttribute(k_sino_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess) return e;
   const int rs = optin, cs = optin;
   if ((e = cudaFuncSetAttribute(k_rows_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_rows_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
@@ -605,7 +720,7 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
   hook(-1, st);
   ImageSource isrc{image, p.N};
   k_prefilter<ImageSource><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows), kThreads, 0, st>>>(
-      p, isrc, p.N, p.N, p.coef_img, p.img_pitch, kPad, p.use_tex ? p.surf_img : 0);
+      p, isrc, p.N, p.N, p.use_tex ? nullptr : p.coef_img, p.img_pitch, kPad, p.use_tex ? p.surf_img : 0);
   hook(0, st);
   k_rows_fwd<false><<<dim3(p.nh, p.M), kThreads, rows_fwd_smem(p), st>>>(p);
   hook(1, st);
@@ -629,6 +744,12 @@ cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image
   return cudaGetLastError();
 }
 
-cudaError_t launch_sino_filter(const DevPlan&, const float*, float*, cudaStream_t) { return cudaErrorNotSupported; }
+cudaError_t launch_fbp(const DevPlan& p, const float* sino, float* image, int filter, cudaStream_t st, StageHook hook) {
+  hook(-1, st);
+  k_sino_filter<<<p.n_angles, kThreads, filt_smem(p), st>>>(p, sino, p.filt + static_cast<size_t>(filter) * (p.n_filt / 2 + 1),
+                                                           p.sino_tmp);
+  hook(10, st);
+  return launch_backproject(p, p.sino_tmp, image, st, hook);
+}
 
 }  // namespace radon

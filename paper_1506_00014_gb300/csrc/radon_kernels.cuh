@@ -40,19 +40,22 @@ struct DevPlan {
   const int4* bp_anc;  // 2 int4 per (m, tile)
   const float2* bp_m;
   const float* fir;    // kFirHalf + 1
-  const float* filt;   // FBP transfer function (n_filt_c complex bins) or null
+  const float* filt;   // FBP transfer functions / n_filt: 3 tables of n_filt/2 + 1 real bins
   // scratch
   float* coef_img;     // (N + 2 kPad)^2, zero border
   int use_tex;         // 1: the forward sampling reads the coefficient image through tex_img
   cudaTextureObject_t tex_img;   // N x N CUDA array holding Q f (border mode: zero outside)
   cudaSurfaceObject_t surf_img;  // write view of the same array (filled by the pre-filter)
+  cudaTextureObject_t tex_lp;    // log-polar coefficients, M (nh + 4) rows x y_pitch columns
+  cudaSurfaceObject_t surf_lp;   // write view (filled by the inverse rho FFT)
   int rows_tw_smem;    // 1: row kernels stage the rho twiddles in shared memory
   float* coef_sino;    // n_angles x sino_pitch, zero border
   float2* xspec;       // M x nh x x_pitch
   float2* yspec;       // M x (nh + 4) x x_pitch
   float* ylp;          // M x (nh + 4) x y_pitch
   float* sino_tmp;     // n_angles x n_det (filtered sinogram for FBP)
-  int n_filt, filt_pitch;  // FBP: padded FFT length along s and spectrum pitch
+  int n_filt;          // FBP: zero-padded real FFT length along s
+  int filt_tw_smem;    // 1: the FBP row kernel stages its twiddles in shared memory
   RadixList rad_filt;
   const float2* tw_filt;
   const float2* tw_filt_r2c;
@@ -71,7 +74,7 @@ struct StageHook {
 // Each returns cudaGetLastError() after its launches.
 cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cudaStream_t st, StageHook hook);
 cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook);
-cudaError_t launch_sino_filter(const DevPlan& p, const float* sino, float* out, cudaStream_t st);
+cudaError_t launch_fbp(const DevPlan& p, const float* sino, float* image, int filter, cudaStream_t st, StageHook hook);
 
 // Dynamic shared memory limits are raised once per device.
 cudaError_t configure_kernels(DevPlan& p);

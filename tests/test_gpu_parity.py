@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import direct, geometry, kernels, logpolar
+from oracle import direct, fbp, geometry, kernels, logpolar
 from workloads import ellipse_image, gaussian_image, random_ellipses, random_sinogram, smooth_random_image
 
 torch = pytest.importorskip("torch")
@@ -106,6 +106,28 @@ def test_backprojection_matches_logpolar_oracle(rl, N, na, nd, interp, M):
         assert _rel(got, ref) < TOL, _rel(got, ref)
 
 
+def _gpu_fbp(rl, plan, g, kind):
+    gd = torch.tensor(np.asarray(g, dtype=np.float32), device="cuda")
+    out = torch.full(plan.image_shape, float("nan"), dtype=torch.float32, device="cuda")
+    rl.radon_fbp(plan, gd, out, kind)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("N,na,nd,interp,M", CASES[:5])
+def test_fbp_matches_oracle(rl, N, na, nd, interp, M):
+    geo = geometry.make_geometry(N, na, nd, M, interp)
+    plan = rl.radon_plan_create(N, na, nd, interp, M)
+    K = kernels.multiplier(geo, "B")
+    dft = logpolar._Dft(geo)
+    g = random_sinogram(na, nd, 31)
+    for kind, name in enumerate(fbp.FILTERS):
+        ref = fbp.fbp(_f32(g), geo, name, K=K, dft=dft)
+        got = _gpu_fbp(rl, plan, g, kind)
+        assert np.all(np.isfinite(got))
+        assert _rel(got, ref) < TOL, (name, _rel(got, ref))
+
+
 def test_zero_and_out_of_support_inputs_give_exact_zeros(rl):
     N, na, nd = 64, 64, 96
     plan = rl.radon_plan_create(N, na, nd, 3, 3)
@@ -193,6 +215,15 @@ def test_full_size_backprojection_matches_oracle(rl, full_geo, interp):
     g = random_sinogram(2048, 3072, 3)
     got = _gpu_back(rl, plan, g)
     ref = logpolar.backproject(_f32(g), geo)
+    assert _rel(got, ref) < TOL, _rel(got, ref)
+
+
+def test_full_size_fbp_matches_oracle(rl, full_geo):
+    geo = full_geo[3]
+    plan = rl.radon_plan_create(2048, 2048, 3072, 3, 3)
+    g = random_sinogram(2048, 3072, 7)
+    got = _gpu_fbp(rl, plan, g, 1)
+    ref = fbp.fbp(_f32(g), geo, "shepp-logan")
     assert _rel(got, ref) < TOL, _rel(got, ref)
 
 
