@@ -1,0 +1,79 @@
+"""torch.autograd wrappers: R with backward R#, and R# with backward R.
+
+With torch's plain sums, <R f, g> = sum_ak (R f)_ak g_ak approximates (1 / (dtheta ds)) times
+the continuous inner product, and <f, R# g> = sum_p f_p (R# g)_p approximates (1 / dx^2) times
+its continuous counterpart.  So the gradient of sum (R f) * G with respect to f is
+(dx^2 / (dtheta ds)) R# G, and that of sum (R# g) * F with respect to g is (dtheta ds / dx^2) R F.
+Here dx = 2/N, dtheta = pi/n_angles and ds = 2 sqrt(2)/n_det.
+
+R# is the discretised adjoint of the continuous R (Algorithm 2), not the transpose of the discrete
+Algorithm 1. The two agree to about 1e-5 relative on smooth inputs and differ more on rough
+ones, and that difference is what a finite-difference check of these gradients measures.
+
+R is linear, so nothing is saved for backward.  Inputs of shape [N, N] / [n_angles, n_det] or
+batches [B, ...] of them; each slice is one C ABI call on the current stream.
+"""
+
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import binding
+
+
+def adjoint_scales(plan: binding.RadonPlan):
+    """(c_R, c_B): grad of R is c_R * R#, grad of R# is c_B * R."""
+    info = plan.info
+    dx2 = (2.0 / info["N"]) ** 2
+    dsino = (math.pi / info["n_angles"]) * (2.0 * math.sqrt(2.0) / info["n_det"])
+    return dx2 / dsino, dsino / dx2
+
+
+def _apply(fn, plan, x, out_shape):
+    x = x.contiguous()
+    if x.dim() == 2:
+        out = torch.empty(out_shape, dtype=torch.float32, device=x.device)
+        fn(plan, x, out)
+        return out
+    out = torch.empty((x.shape[0],) + tuple(out_shape), dtype=torch.float32, device=x.device)
+    for b in range(x.shape[0]):
+        fn(plan, x[b], out[b])
+    return out
+
+
+class RadonFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, image, plan):
+        ctx.plan = plan
+        return _apply(binding.radon_forward, plan, image, plan.sino_shape)
+
+    @staticmethod
+    def backward(ctx, grad):
+        plan = ctx.plan
+        c_r, _ = adjoint_scales(plan)
+        return _apply(binding.radon_backproject, plan, grad, plan.image_shape) * c_r, None
+
+
+class BackprojectFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, sino, plan):
+        ctx.plan = plan
+        return _apply(binding.radon_backproject, plan, sino, plan.image_shape)
+
+    @staticmethod
+    def backward(ctx, grad):
+        plan = ctx.plan
+        _, c_b = adjoint_scales(plan)
+        return _apply(binding.radon_forward, plan, grad, plan.sino_shape) * c_b, None
+
+
+def radon(image: torch.Tensor, plan: binding.RadonPlan) -> torch.Tensor:
+    """R f for [N, N] or [B, N, N] float32 CUDA tensors (differentiable)."""
+    return RadonFunction.apply(image, plan)
+
+
+def backproject(sino: torch.Tensor, plan: binding.RadonPlan) -> torch.Tensor:
+    """R# g for [n_angles, n_det] or [B, n_angles, n_det] float32 CUDA tensors (differentiable)."""
+    return BackprojectFunction.apply(sino, plan)

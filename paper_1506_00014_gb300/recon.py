@@ -1,0 +1,112 @@
+"""Iterative reconstructions on top of R and R# (Section 8 of the paper): everything stays on
+the GPU between the initial upload and the final result.
+
+least_squares: gradient descent on ||R f - g||^2 with the gradient 2 c_R R#(R f - g) (the
+    autograd.RadonFunction backward).  The step is 1 / L, with L estimated by power iteration on
+    the normal operator c_R R# R.  Optionally one iteration is captured in a CUDA graph and
+    replayed.
+em: f <- f * R#(g / R f) / R# chi_C (Section 8), chi_C the indicator of the lines that meet the
+    unit disc (bins with |s| < 1).
+"""
+
+from __future__ import annotations
+
+import torch
+
+from . import binding
+from .autograd import adjoint_scales
+
+
+def _fwd(plan, f, out):
+    binding.radon_forward(plan, f, out)
+    return out
+
+
+def _bp(plan, g, out):
+    binding.radon_backproject(plan, g, out)
+    return out
+
+
+def normal_operator_norm(plan: binding.RadonPlan, iters: int = 20, seed: int = 0) -> float:
+    """Largest eigenvalue of c_R R# R by power iteration (R# R is close to self-adjoint)."""
+    c_r, _ = adjoint_scales(plan)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    x = torch.randn(plan.image_shape, device="cuda", generator=gen)
+    s = torch.empty(plan.sino_shape, device="cuda")
+    y = torch.empty(plan.image_shape, device="cuda")
+    lam = 0.0
+    for _ in range(iters):
+        x = x / x.norm()
+        _bp(plan, _fwd(plan, x, s), y)
+        y.mul_(c_r)
+        lam = float(torch.dot(x.flatten(), y.flatten()))
+        x = y.clone()
+    return lam
+
+
+class LeastSquares:
+    """Gradient descent x <- x - step * 2 c_R R#(R x - g), optionally replayed from a CUDA graph."""
+
+    def __init__(self, plan: binding.RadonPlan, g: torch.Tensor, step: float | None = None, f0=None,
+                 use_graph: bool = False):
+        self.plan = plan
+        self.g = g.contiguous()
+        self.c_r, _ = adjoint_scales(plan)
+        if step is None:
+            step = 1.0 / (2.0 * normal_operator_norm(plan))
+        self.step = float(step)
+        self.f = torch.zeros(plan.image_shape, device="cuda") if f0 is None else f0.clone().contiguous()
+        self.r = torch.empty(plan.sino_shape, device="cuda")
+        self.grad = torch.empty(plan.image_shape, device="cuda")
+        self.graph = None
+        if use_graph:
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                for _ in range(2):  # warm up outside the capture
+                    self._iterate(dry=True)
+            torch.cuda.current_stream().wait_stream(side)
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._iterate()
+
+    def _iterate(self, dry: bool = False):
+        _fwd(self.plan, self.f, self.r)
+        self.r.sub_(self.g)
+        _bp(self.plan, self.r, self.grad)
+        if not dry:
+            self.f.add_(self.grad, alpha=-2.0 * self.c_r * self.step)
+
+    def run(self, steps: int):
+        for _ in range(steps):
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._iterate()
+        return self.f
+
+    def loss(self) -> float:
+        _fwd(self.plan, self.f, self.r)
+        return float(((self.r - self.g) ** 2).sum())
+
+
+def em(plan: binding.RadonPlan, g: torch.Tensor, iters: int, f0=None, eps: float = 1e-12) -> torch.Tensor:
+    """Expectation-maximisation for non-negative f and data g >= 0 (Section 8)."""
+    info = plan.info
+    nd = info["n_det"]
+    k = torch.arange(nd, device="cuda")
+    live = (2 * (2 * k - nd) ** 2 < nd * nd).to(torch.float32)
+    chi = live.expand(info["n_angles"], nd).contiguous()
+    norm = torch.empty(plan.image_shape, device="cuda")
+    _bp(plan, chi, norm)
+    disc = norm > eps
+    f = torch.where(disc, torch.ones(plan.image_shape, device="cuda"), torch.zeros(plan.image_shape, device="cuda")) \
+        if f0 is None else f0.clone().contiguous()
+    r = torch.empty(plan.sino_shape, device="cuda")
+    back = torch.empty(plan.image_shape, device="cuda")
+    for _ in range(iters):
+        _fwd(plan, f, r)
+        ratio = torch.where(r > eps, g / r.clamp_min(eps), torch.zeros_like(r)) * chi
+        _bp(plan, ratio.contiguous(), back)
+        f = torch.where(disc, f * back / norm.clamp_min(eps), torch.zeros_like(f))
+    return f

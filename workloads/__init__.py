@@ -9,6 +9,7 @@ from .phantoms import (  # noqa: F401
     Ellipse,
     random_ellipses,
     ellipse_image,
+    ellipse_sinogram,
     gaussian_image,
     random_sinogram,
     smooth_random_image,

@@ -107,6 +107,21 @@ def random_sinogram(n_angles: int, n_det: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal((n_angles, n_det))
 
 
+def ellipse_sinogram(ellipses: list[Ellipse], n_angles: int, n_det: int) -> np.ndarray:
+    """Line integrals of the ellipse indicators on the sinogram grid theta_a = a pi / n_angles,
+    s_k = (k - n_det/2) 2 sqrt(2) / n_det (chord length of each ellipse times its density)."""
+    th = (np.arange(n_angles) * np.pi / n_angles)[:, None]
+    s = ((np.arange(n_det) - n_det / 2) * (2.0 * np.sqrt(2.0) / n_det))[None, :]
+    out = np.zeros((n_angles, n_det))
+    for e in ellipses:
+        c, sn = np.cos(th - e.psi), np.sin(th - e.psi)
+        half2 = (e.a * c) ** 2 + (e.b * sn) ** 2  # squared support half-width along s
+        t = s - (e.cx * np.cos(th) + e.cy * np.sin(th))
+        chord = np.where(t * t < half2, 2.0 * e.a * e.b * np.sqrt(np.maximum(half2 - t * t, 0.0)) / half2, 0.0)
+        out += e.density * chord
+    return out
+
+
 def slice_sizes(count: int, seed: int, choices=(256, 512, 1024, 2048, 4096)) -> list[int]:
     """Uneven slice sizes N drawn uniformly from ``choices``."""
     rng = np.random.default_rng(seed)
