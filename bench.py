@@ -138,6 +138,22 @@ def stage_bytes(info):
     }
 
 
+def reduce_max(value: float, dist, device) -> float:
+    """Max over ranks of a per-rank scalar (identity without a process group)."""
+    if dist is None or not dist.is_available() or not dist.is_initialized():
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_step: int, steps: int, max_seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling)."""
+    return world * units_per_step * steps / max_seconds
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -211,13 +227,9 @@ def run_ours(args):
     clk = clocks.stop()
     stage = rl.radon_profile_read(plan)
     rl.radon_profile_enable(plan, False)
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev), dist if world > 1 else None, dev)
     ms_per_step = total_ms / args.steps
-    value = world * _samples_per_step() * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(world, _samples_per_step(), args.steps, total_ms / 1e3)
 
     # roofline of the dominant stage
     nbytes = stage_bytes(info)
@@ -249,13 +261,9 @@ def run_ours(args):
     for _ in range(args.steps):
         rl.radon_forward_host(plan, h_f, h_s, stream)
         rl.radon_backproject_host(plan, h_g, h_i, stream)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(time.perf_counter() - t0, dist if world > 1 else None, dev)
     e2e = {
-        "value": world * _samples_per_step() * args.steps / e2e_s,
+        "value": whole_job_rate(world, _samples_per_step(), args.steps, e2e_s),
         "unit": UNIT,
         "h2d_bytes_per_step": 4 * (N * N + N_ANGLES * N_DET),
         "d2h_bytes_per_step": 4 * (N_ANGLES * N_DET + N * N),

@@ -64,6 +64,7 @@ typedef struct {
   int r;              /* fine angular sub-samples per coarse angle (Omega_lp -> Omega_p)       */
   int n_quad;         /* trapezoid nodes used for the kernel integrals (Eq. weightsa)          */
   int n_filter;       /* zero-padded FFT length of the FBP filter along s (>= 2 n_det)          */
+  int column_group;   /* rho frequencies per CTA of the theta convolution (performance knob)    */
   double beta, a_R, a_r, L;       /* pi/M, Eq. aconst, L = -log(a_r)                           */
   double d_phi, d_rho, d_s, d_theta;
   size_t device_bytes;            /* device memory owned by the plan (tables + scratch)        */
@@ -99,6 +100,21 @@ int radon_backproject(radon_plan plan, const float* d_sino, float* d_image, void
  * cos(pi sigma / (2 sigma_max)) (cosine, Eq. cosfilt), sigma_max = 1/(2 ds).  Then R# is applied.
  * d_sino is not modified; the filtered sinogram lives in plan-owned memory. */
 int radon_fbp(radon_plan plan, const float* d_sino, float* d_image, int filter, void* stream);
+
+/* Batches of same-size slices.  radon_plan_reserve_batch makes the plan able to process up to
+ * max_batch slices in one call: it allocates scratch and texture storage for them, synchronising
+ * the device (call it before any stream capture).  It returns RADON_NOT_SUPPORTED when the
+ * stacked slices exceed the device's 2-D surface height.  radon_forward_batch /
+ * radon_backproject_batch then transform `batch` <= max_batch slices stored back to back
+ * ([batch][N][N] images, [batch][n_angles][n_det] sinograms) with the same five kernel launches
+ * as one slice; results equal those of per-slice calls. */
+int radon_plan_reserve_batch(radon_plan plan, int max_batch);
+int radon_forward_batch(radon_plan plan, const float* d_images, float* d_sinos, int batch, void* stream);
+int radon_backproject_batch(radon_plan plan, const float* d_sinos, float* d_images, int batch, void* stream);
+
+/* Number of rho frequencies (1, 2 or 4) one CTA of the theta convolution transforms.  A pure
+ * performance knob (results are unchanged); RADON_NOT_SUPPORTED if the value does not fit. */
+int radon_plan_set_column_group(radon_plan plan, int group);
 
 /* Same as radon_forward / radon_backproject but with HOST buffers: the call copies the input to
  * plan-owned device memory, runs the transform on `stream` and copies the result back; it

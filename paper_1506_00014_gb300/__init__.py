@@ -12,9 +12,11 @@ from .binding import (  # noqa: F401
     RadonPlan,
     load,
     radon_backproject,
+    radon_backproject_batch,
     radon_backproject_host,
     radon_fbp,
     radon_forward,
+    radon_forward_batch,
     radon_forward_host,
     radon_forward_static_scratch,
     radon_geometry,
@@ -22,6 +24,8 @@ from .binding import (  # noqa: F401
     radon_plan_create,
     radon_plan_destroy,
     radon_plan_get_info,
+    radon_plan_reserve_batch,
+    radon_plan_set_column_group,
     radon_profile_enable,
     radon_profile_read,
     radon_status_string,

@@ -22,7 +22,7 @@ class radon_plan_info(ctypes.Structure):
     _fields_ = [
         ("N", _c_int), ("n_angles", _c_int), ("n_det", _c_int), ("interp_order", _c_int),
         ("n_partitions", _c_int), ("N_rho", _c_int), ("n_theta_half", _c_int), ("n_theta", _c_int),
-        ("r", _c_int), ("n_quad", _c_int), ("n_filter", _c_int),
+        ("r", _c_int), ("n_quad", _c_int), ("n_filter", _c_int), ("column_group", _c_int),
         ("beta", ctypes.c_double), ("a_R", ctypes.c_double), ("a_r", ctypes.c_double), ("L", ctypes.c_double),
         ("d_phi", ctypes.c_double), ("d_rho", ctypes.c_double), ("d_s", ctypes.c_double),
         ("d_theta", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
@@ -38,7 +38,8 @@ EXPORTED = (
     "radon_plan_create", "radon_plan_destroy", "radon_plan_get_info", "radon_forward",
     "radon_backproject", "radon_fbp", "radon_forward_host", "radon_backproject_host",
     "radon_geometry", "radon_kernel_quadrant", "radon_status_string", "radon_profile_enable",
-    "radon_profile_read", "radon_forward_static_scratch",
+    "radon_profile_read", "radon_forward_static_scratch", "radon_plan_reserve_batch",
+    "radon_forward_batch", "radon_backproject_batch", "radon_plan_set_column_group",
 )
 
 RADON_NUM_STAGES = 11
@@ -80,6 +81,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.radon_fbp.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_void_p]
     lib.radon_geometry.argtypes = [_c_int, _c_int, _c_int, _c_int, _c_int, P(radon_plan_info)]
     lib.radon_kernel_quadrant.argtypes = [_c_int, _c_int, _c_int, _c_int, _c_int, P(ctypes.c_double)]
+    lib.radon_plan_reserve_batch.argtypes = [_c_void_p, _c_int]
+    lib.radon_plan_set_column_group.argtypes = [_c_void_p, _c_int]
+    for name in ("radon_forward_batch", "radon_backproject_batch"):
+        getattr(lib, name).argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_void_p]
     lib.radon_profile_enable.argtypes = [_c_void_p, _c_int]
     lib.radon_profile_read.argtypes = [_c_void_p, P(ctypes.c_double), P(_c_int)]
     lib.radon_status_string.argtypes = [_c_int]
@@ -245,3 +250,31 @@ def radon_profile_read(plan: RadonPlan):
     n = (_c_int * RADON_NUM_STAGES)()
     _check(load().radon_profile_read(plan.handle, ms, n), "radon_profile_read")
     return {STAGE_NAMES[i]: (ms[i], n[i]) for i in range(RADON_NUM_STAGES)}
+
+
+def radon_plan_reserve_batch(plan: RadonPlan, max_batch: int):
+    _check(load().radon_plan_reserve_batch(plan.handle, int(max_batch)), "radon_plan_reserve_batch")
+    plan.info = radon_plan_get_info(plan)
+
+
+def radon_plan_set_column_group(plan: RadonPlan, group: int):
+    _check(load().radon_plan_set_column_group(plan.handle, int(group)), "radon_plan_set_column_group")
+    plan.info = radon_plan_get_info(plan)
+
+
+def radon_forward_batch(plan: RadonPlan, images, sinos, stream=None):
+    """images [B, N, N] -> sinos [B, n_angles, n_det] (contiguous float32 CUDA tensors)."""
+    b = images.shape[0]
+    _check(load().radon_forward_batch(plan.handle, _dev(images, (b,) + plan.image_shape, "images"),
+                                      _dev(sinos, (b,) + plan.sino_shape, "sinos"), b, _stream(stream, images)),
+           "radon_forward_batch")
+    return sinos
+
+
+def radon_backproject_batch(plan: RadonPlan, sinos, images, stream=None):
+    """sinos [B, n_angles, n_det] -> images [B, N, N] (contiguous float32 CUDA tensors)."""
+    b = sinos.shape[0]
+    _check(load().radon_backproject_batch(plan.handle, _dev(sinos, (b,) + plan.sino_shape, "sinos"),
+                                          _dev(images, (b,) + plan.image_shape, "images"), b, _stream(stream, sinos)),
+           "radon_backproject_batch")
+    return images

@@ -100,6 +100,22 @@ radon::StageHook hook_of(radon_plan_s* p) {
   return h;
 }
 
+// Frees the scratch buffer and the texture storage (the device must be idle).
+void release_scratch(radon_plan_s* p) {
+  radon::DevPlan& d = p->dp;
+  if (d.tex_img) cudaDestroyTextureObject(d.tex_img);
+  if (d.surf_img) cudaDestroySurfaceObject(d.surf_img);
+  if (d.tex_lp) cudaDestroyTextureObject(d.tex_lp);
+  if (d.surf_lp) cudaDestroySurfaceObject(d.surf_lp);
+  if (p->img_array) cudaFreeArray(p->img_array);
+  if (p->lp_array) cudaFreeArray(p->lp_array);
+  if (p->scratch_mem) cudaFree(p->scratch_mem);
+  d.tex_img = d.tex_lp = 0;
+  d.surf_img = d.surf_lp = 0;
+  p->img_array = p->lp_array = nullptr;
+  p->scratch_mem = nullptr;
+}
+
 // A width x height float CUDA array with a point-sampled, zero-border texture and a surface.
 cudaError_t make_texture(int width, int height, cudaArray_t* arr, cudaTextureObject_t* tex, cudaSurfaceObject_t* surf) {
   cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
@@ -119,6 +135,94 @@ cudaError_t make_texture(int width, int height, cudaArray_t* arr, cudaTextureObj
   e = cudaCreateTextureObject(tex, &rd, &td, nullptr);
   if (e == cudaSuccess) e = cudaCreateSurfaceObject(surf, &rd);
   return e;
+}
+
+// Scratch buffers and texture storage for `cap` same-size slices; replaces the previous ones.
+// Slice b of a batch uses the buffers at offset b * (per-slice size); its image-texture rows are
+// [b (N + kTexGap), b (N + kTexGap) + N) with kTexGap zero rows after them.
+cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
+  radon::DevPlan& d = p->dp;
+  const int N = d.N, na = d.n_angles, nd = d.n_det;
+  const size_t nrow = static_cast<size_t>(d.nh) + radon::kHaloLo + radon::kHaloHi;
+  const size_t e_img = static_cast<size_t>(d.img_pitch) * d.img_pitch;
+  const size_t e_sino = static_cast<size_t>(na) * d.sino_pitch;
+  const size_t e_x = static_cast<size_t>(d.M) * d.nh * d.x_pitch;
+  const size_t e_ys = static_cast<size_t>(d.M) * nrow * d.x_pitch;
+  const size_t e_y = static_cast<size_t>(d.M) * nrow * d.y_pitch;
+  const int img_rows = N + radon::kTexGap;
+  const long long tex_img_h = static_cast<long long>(cap) * img_rows;
+  const long long tex_lp_h = static_cast<long long>(cap) * d.M * static_cast<long long>(nrow);
+  int dev = 0, max_h = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxSurface2DHeight, dev);
+  if (e != cudaSuccess) return e;
+  if (cap < 1 || tex_img_h > max_h || tex_lp_h > max_h) return cudaErrorInvalidValue;
+  size_t sc = 0;
+  auto take = [&](size_t bytes) {
+    const size_t off = sc;
+    sc = align_up(sc + bytes, 256);
+    return off;
+  };
+  const size_t s_img = take(sizeof(float) * e_img * cap);
+  const size_t s_sino = take(sizeof(float) * e_sino * cap);
+  const size_t s_x = take(sizeof(float2) * e_x * cap);
+  const size_t s_ys = take(sizeof(float2) * e_ys * cap);
+  const size_t s_y = take(sizeof(float) * e_y * cap);
+  const size_t s_ftmp = take(sizeof(float) * static_cast<size_t>(na) * nd);
+  const size_t s_io_img = take(sizeof(float) * static_cast<size_t>(N) * N);
+  const size_t s_io_sino = take(sizeof(float) * static_cast<size_t>(na) * nd);
+  void* mem = nullptr;
+  cudaArray_t img_arr = nullptr, lp_arr = nullptr;
+  cudaTextureObject_t tex_img = 0, tex_lp = 0;
+  cudaSurfaceObject_t surf_img = 0, surf_lp = 0;
+  e = cudaMalloc(&mem, sc);
+  if (e == cudaSuccess) e = cudaMemset(mem, 0, sc);
+  if (e == cudaSuccess) e = make_texture(N, static_cast<int>(tex_img_h), &img_arr, &tex_img, &surf_img);
+  if (e == cudaSuccess) e = make_texture(d.y_pitch, static_cast<int>(tex_lp_h), &lp_arr, &tex_lp, &surf_lp);
+  // the arrays start undefined: copy zeros (the fresh scratch) into them
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DToArray(img_arr, 0, 0, mem, sizeof(float) * N, sizeof(float) * N, tex_img_h, cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DToArray(lp_arr, 0, 0, static_cast<char*>(mem) + s_y, sizeof(float) * d.y_pitch,
+                            sizeof(float) * d.y_pitch, tex_lp_h, cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) {
+    if (tex_img) cudaDestroyTextureObject(tex_img);
+    if (surf_img) cudaDestroySurfaceObject(surf_img);
+    if (tex_lp) cudaDestroyTextureObject(tex_lp);
+    if (surf_lp) cudaDestroySurfaceObject(surf_lp);
+    if (img_arr) cudaFreeArray(img_arr);
+    if (lp_arr) cudaFreeArray(lp_arr);
+    cudaFree(mem);
+    return e;
+  }
+  release_scratch(p);
+  char* sb = static_cast<char*>(mem);
+  p->scratch_mem = mem;
+  p->img_array = img_arr;
+  p->lp_array = lp_arr;
+  d.tex_img = tex_img;
+  d.surf_img = surf_img;
+  d.tex_lp = tex_lp;
+  d.surf_lp = surf_lp;
+  d.use_tex = 1;
+  d.coef_img = reinterpret_cast<float*>(sb + s_img);
+  d.coef_sino = reinterpret_cast<float*>(sb + s_sino);
+  d.xspec = reinterpret_cast<float2*>(sb + s_x);
+  d.yspec = reinterpret_cast<float2*>(sb + s_ys);
+  d.ylp = reinterpret_cast<float*>(sb + s_y);
+  d.sino_tmp = reinterpret_cast<float*>(sb + s_ftmp);
+  d.bs_img = e_img;
+  d.bs_sino = e_sino;
+  d.bs_x = e_x;
+  d.bs_ys = e_ys;
+  d.bs_y = e_y;
+  d.tex_img_rows = img_rows;
+  d.batch_cap = cap;
+  p->io_image = reinterpret_cast<float*>(sb + s_io_img);
+  p->io_sino = reinterpret_cast<float*>(sb + s_io_sino);
+  p->info.device_bytes = p->table_bytes + sc + sizeof(float) * (static_cast<size_t>(N) * tex_img_h +
+                                                                 static_cast<size_t>(d.y_pitch) * tex_lp_h);
+  return cudaSuccess;
 }
 
 bool on_plan_device(const radon_plan_s* p) {
@@ -163,14 +267,8 @@ void radon_plan_destroy(radon_plan plan) {
   if (!plan) return;
   cudaDeviceSynchronize();
   for (cudaEvent_t ev : plan->prof_pool) cudaEventDestroy(ev);
-  if (plan->dp.tex_img) cudaDestroyTextureObject(plan->dp.tex_img);
-  if (plan->dp.surf_img) cudaDestroySurfaceObject(plan->dp.surf_img);
-  if (plan->img_array) cudaFreeArray(plan->img_array);
-  if (plan->dp.tex_lp) cudaDestroyTextureObject(plan->dp.tex_lp);
-  if (plan->dp.surf_lp) cudaDestroySurfaceObject(plan->dp.surf_lp);
-  if (plan->lp_array) cudaFreeArray(plan->lp_array);
+  release_scratch(plan);
   cudaFree(plan->table_mem);
-  cudaFree(plan->scratch_mem);
   delete plan;
 }
 
@@ -247,33 +345,14 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   const size_t o_banc = tp.add(t.bp_anc), o_bm = tp.add(t.bp_m), o_fir = tp.add(t.fir);
   const size_t o_twf = tp.add(t.tw_filt), o_twfr = tp.add(t.tw_filt_r2c), o_filt = tp.add(t.filt);
 
-  const size_t nrow = static_cast<size_t>(d.nh) + radon::kHaloLo + radon::kHaloHi;
-  size_t sc = 0;
-  auto take = [&](size_t bytes) {
-    const size_t off = sc;
-    sc = align_up(sc + bytes, 256);
-    return off;
-  };
-  const size_t s_img = take(sizeof(float) * static_cast<size_t>(d.img_pitch) * d.img_pitch);
-  const size_t s_sino = take(sizeof(float) * static_cast<size_t>(n_angles) * d.sino_pitch);
-  const size_t s_x = take(sizeof(float2) * static_cast<size_t>(d.M) * d.nh * d.x_pitch);
-  const size_t s_ys = take(sizeof(float2) * static_cast<size_t>(d.M) * nrow * d.x_pitch);
-  const size_t s_y = take(sizeof(float) * static_cast<size_t>(d.M) * nrow * d.y_pitch);
-  const size_t s_ftmp = take(sizeof(float) * static_cast<size_t>(n_angles) * n_det);
-  const size_t s_io_img = take(sizeof(float) * static_cast<size_t>(N) * N);
-  const size_t s_io_sino = take(sizeof(float) * static_cast<size_t>(n_angles) * n_det);
-
   cudaError_t e = cudaMalloc(&p->table_mem, tp.total());
   if (e == cudaSuccess) e = tp.upload(p->table_mem);
-  if (e == cudaSuccess) e = cudaMalloc(&p->scratch_mem, sc);
-  if (e == cudaSuccess) e = cudaMemset(p->scratch_mem, 0, sc);
   if (e != cudaSuccess) {
     cudaGetLastError();
     radon_plan_destroy(p);
     return status_of(e);
   }
   char* tb = static_cast<char*>(p->table_mem);
-  char* sb = static_cast<char*>(p->scratch_mem);
   d.tw_rho = reinterpret_cast<const float2*>(tb + o_tw_rho);
   d.tw_r2c = reinterpret_cast<const float2*>(tb + o_tw_r2c);
   d.tw_th = reinterpret_cast<const float2*>(tb + o_tw_th);
@@ -294,35 +373,20 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.tw_filt = reinterpret_cast<const float2*>(tb + o_twf);
   d.tw_filt_r2c = reinterpret_cast<const float2*>(tb + o_twfr);
   d.filt = reinterpret_cast<const float*>(tb + o_filt);
-  d.sino_tmp = reinterpret_cast<float*>(sb + s_ftmp);
-  d.coef_img = reinterpret_cast<float*>(sb + s_img);
-  d.coef_sino = reinterpret_cast<float*>(sb + s_sino);
-  d.xspec = reinterpret_cast<float2*>(sb + s_x);
-  d.yspec = reinterpret_cast<float2*>(sb + s_ys);
-  d.ylp = reinterpret_cast<float*>(sb + s_y);
-  p->io_image = reinterpret_cast<float*>(sb + s_io_img);
-  p->io_sino = reinterpret_cast<float*>(sb + s_io_sino);
-  p->info.device_bytes = tp.total() + sc;
-
-  // The coefficient image and the log-polar coefficients also live in CUDA arrays, read with
-  // tex2Dgather (border mode: zero outside) and written through surfaces.
-  {
-    const int lp_rows = static_cast<int>(d.M * nrow);
-    e = make_texture(N, N, &p->img_array, &d.tex_img, &d.surf_img);
-    if (e == cudaSuccess) e = make_texture(d.y_pitch, lp_rows, &p->lp_array, &d.tex_lp, &d.surf_lp);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      radon_plan_destroy(p);
-      return status_of(e);
-    }
-    d.use_tex = 1;
-    p->info.device_bytes += sizeof(float) * (static_cast<size_t>(N) * N + static_cast<size_t>(d.y_pitch) * lp_rows);
-  }
-  e = radon::configure_kernels(d);
+  p->table_bytes = tp.total();
+  e = allocate_scratch(p, 1);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     radon_plan_destroy(p);
     return status_of(e);
   }
+  e = radon::configure_kernels(d);
+  if (e != cudaSuccess) {  // cudaErrorInvalidValue: a kernel's shared memory would exceed the device limit
+    cudaGetLastError();
+    radon_plan_destroy(p);
+    return e == cudaErrorInvalidValue ? RADON_NOT_SUPPORTED : status_of(e);
+  }
+  p->info.column_group = d.col_group;
   *out = p;
   return RADON_OK;
 }
@@ -380,6 +444,43 @@ int radon_backproject_host(radon_plan plan, const float* h_sino, float* h_image,
                         cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return status_of(e);
+}
+
+int radon_plan_reserve_batch(radon_plan plan, int max_batch) {
+  if (!plan || max_batch < 1) return RADON_INVALID_ARG;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  if (max_batch <= plan->dp.batch_cap) return RADON_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = allocate_scratch(plan, max_batch);
+  if (e == cudaErrorInvalidValue) return RADON_NOT_SUPPORTED;
+  return status_of(e);
+}
+
+int radon_forward_batch(radon_plan plan, const float* d_images, float* d_sinos, int batch, void* stream) {
+  if (!plan || !d_images || !d_sinos || batch < 1 || batch > plan->dp.batch_cap) return RADON_INVALID_ARG;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  return status_of(
+      radon::launch_forward(plan->dp, d_images, d_sinos, static_cast<cudaStream_t>(stream), hook_of(plan), batch));
+}
+
+int radon_backproject_batch(radon_plan plan, const float* d_sinos, float* d_images, int batch, void* stream) {
+  if (!plan || !d_images || !d_sinos || batch < 1 || batch > plan->dp.batch_cap) return RADON_INVALID_ARG;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  return status_of(
+      radon::launch_backproject(plan->dp, d_sinos, d_images, static_cast<cudaStream_t>(stream), hook_of(plan), batch));
+}
+
+int radon_plan_set_column_group(radon_plan plan, int group) {
+  if (!plan || (group != 1 && group != 2 && group != 4)) return RADON_INVALID_ARG;
+  radon::DevPlan d = plan->dp;
+  d.col_group = group;
+  radon::HostTables t;
+  radon::Radices rad;
+  if (!radon::factor_radices(d.n_theta, &rad) || !copy_radices(rad, group, &d.rad_th)) return RADON_NOT_SUPPORTED;
+  if (radon::configure_kernels(d) != cudaSuccess) return RADON_NOT_SUPPORTED;
+  plan->dp = d;
+  plan->info.column_group = group;
+  return RADON_OK;
 }
 
 int radon_profile_enable(radon_plan plan, int enable) {

@@ -106,6 +106,7 @@ constexpr int kPfInR = kPfRows + 2 * kFirHalf, kPfInC = kPfCols + 2 * kFirHalf;
 struct ImageSource {
   const float* __restrict__ f;
   int N;
+  __device__ __forceinline__ void slice(int b) { f += static_cast<size_t>(b) * N * N; }
   __device__ __forceinline__ bool interior(int r0, int r1, int c0, int c1) const {
     return r0 >= 0 && r1 <= N && c0 >= 0 && c1 <= N;
   }
@@ -128,6 +129,7 @@ struct ImageSource {
 struct SinoSource {
   const float* __restrict__ g;
   int na, nd, live_lo, live_hi;
+  __device__ __forceinline__ void slice(int b) { g += static_cast<size_t>(b) * na * nd; }
   __device__ __forceinline__ bool interior(int r0, int r1, int c0, int c1) const {
     return r0 >= 0 && r1 <= na && c0 >= 0 && c1 <= nd + 1;
   }
@@ -149,9 +151,13 @@ struct SinoSource {
 template <class Src>
 __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int n_rows, int n_cols,
                                                         float* __restrict__ out, int out_pitch, int out_r0,
-                                                        cudaSurfaceObject_t surf) {
+                                                        size_t out_bstride, cudaSurfaceObject_t surf, int surf_rows) {
   __shared__ float s_in[kPfInR][kPfInC + 1];
   __shared__ float s_mid[kPfInR][kPfCols + 1];
+  const int b = blockIdx.z;  // slice of a batch
+  src.slice(b);
+  if (out) out += b * out_bstride;
+  const int srow = b * surf_rows;
   const int r0 = blockIdx.y * kPfRows - kFirHalf, c0 = blockIdx.x * kPfCols - kFirHalf;
   const int tid = threadIdx.x;
   if (src.interior(r0, r0 + kPfInR, c0, c0 + kPfInC)) {
@@ -184,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
       if (orow + ly < n_rows && ocol + lx < n_cols) {
         const float v = s_in[ly + kFirHalf][lx + kFirHalf];
         if (out) out[static_cast<size_t>(orow + ly + out_r0) * out_pitch + ocol + lx + kPad] = v;
-        if (surf) surf2Dwrite(v, surf, (ocol + lx) * static_cast<int>(sizeof(float)), orow + ly);
+        if (surf) surf2Dwrite(v, surf, (ocol + lx) * static_cast<int>(sizeof(float)), srow + orow + ly);
       }
     }
     return;
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
       const int gr = orow + sy + t;
       if (gr < n_rows && gc < n_cols) {
         if (out) out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = acc;
-        if (surf) surf2Dwrite(acc, surf, gc * static_cast<int>(sizeof(float)), gr);
+        if (surf) surf2Dwrite(acc, surf, gc * static_cast<int>(sizeof(float)), srow + gr);
       }
     }
   }
@@ -232,8 +238,8 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
 // Row sampling.
 
 // Value of the image interpolant at padded index coordinates (ic + ac, ir + ar).
-__device__ __forceinline__ float sample_image(const DevPlan& p, int ic, float ac, int ir, float ar) {
-  const float* __restrict__ c = p.coef_img;
+__device__ __forceinline__ float sample_image(const DevPlan& p, int b, int ic, float ac, int ir, float ar) {
+  const float* __restrict__ c = p.coef_img + b * p.bs_img;
   const int pitch = p.img_pitch;
   if (p.interp == 3) {
     if (ic < 1 || ic > pitch - 3 || ir < 1 || ir > pitch - 3) return 0.f;
@@ -301,8 +307,8 @@ __device__ __forceinline__ float sample_image_tex(cudaTextureObject_t tex, int i
   return fmaf(ar, v1 - v0, v0);
 }
 
-__device__ void sample_row_forward(const DevPlan& p, int m, int jj, float* __restrict__ h, float4* __restrict__ anc,
-                                   float2* __restrict__ dir) {
+__device__ void sample_row_forward(const DevPlan& p, int b, int m, int jj, float* __restrict__ h,
+                                   float4* __restrict__ anc, float2* __restrict__ dir) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int r = p.r, ne = p.n_eanc;
   const bool cubic = p.interp == 3;
@@ -334,8 +340,8 @@ __device__ void sample_row_forward(const DevPlan& p, int m, int jj, float* __res
       const float fc = floorf(Fc), fr = floorf(Fr);
       const int ic = static_cast<int>(a.x + fc), ir = static_cast<int>(a.z + fr);  // padded indices
       if (ic < 1 || ic > P - 3 || ir < 1 || ir > P - 3) continue;                 // every tap is zero
-      acc += p.use_tex ? sample_image_tex(p.tex_img, ic - kPad, Fc - fc, ir - kPad, Fr - fr, cubic)
-                       : sample_image(p, ic, Fc - fc, ir, Fr - fr);
+      acc += p.use_tex ? sample_image_tex(p.tex_img, ic - kPad, Fc - fc, ir - kPad + b * p.tex_img_rows, Fr - fr, cubic)
+                       : sample_image(p, b, ic, Fc - fc, ir, Fr - fr);
     }
     if (valid) h[i] = acc * e.x;
   }
@@ -344,7 +350,7 @@ __device__ void sample_row_forward(const DevPlan& p, int m, int jj, float* __res
 // Back-projection: G(phi_j, rho_i) = g~(phi_j + m beta, (e^rho_i - (1 - a_R) cos phi_j) / a_R).
 // The theta taps (rows of the extended sinogram, flips, weights) are the same for the whole row;
 // a flipped row (theta + pi) is read at k -> n_det - k, i.e. with reversed s weights.
-__device__ void sample_row_backproject(const DevPlan& p, int m, int jj, float* __restrict__ h) {
+__device__ void sample_row_backproject(const DevPlan& p, int b, int m, int jj, float* __restrict__ h) {
   const int2 th = p.bp_th[m * p.nh + jj];
   const int2 cj = p.bp_c[jj];
   const float Ft = __int_as_float(th.y), Fc = __int_as_float(cj.y);
@@ -367,7 +373,7 @@ __device__ void sample_row_backproject(const DevPlan& p, int m, int jj, float* _
     int a2 = (t0 + dt) % (2 * na);
     if (a2 < 0) a2 += 2 * na;
     flip[dt] = a2 >= na;
-    rows[dt] = p.coef_sino + static_cast<size_t>(flip[dt] ? a2 - na : a2) * pitch;
+    rows[dt] = p.coef_sino + b * p.bs_sino + static_cast<size_t>(flip[dt] ? a2 - na : a2) * pitch;
   }
   for (int i = threadIdx.x; i < p.N_rho; i += blockDim.x) {
     const int2 ei = p.bp_e[i];
@@ -411,22 +417,22 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
   float2* bufA = smem;
   float2* bufB = smem + nc;
   const float2* tw;
-  const int jj = blockIdx.x, m = blockIdx.y;
+  const int jj = blockIdx.x, m = blockIdx.y, b = blockIdx.z;
   if (BACK) {
     float2* tws = smem + 2 * nc;
     if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
     tw = p.rows_tw_smem ? tws : p.tw_rho;
-    sample_row_backproject(p, m, jj, reinterpret_cast<float*>(bufA));
+    sample_row_backproject(p, b, m, jj, reinterpret_cast<float*>(bufA));
   } else {
     float4* anc = reinterpret_cast<float4*>(smem + fwd_anchor_offset(p));
     float2* tws = smem + fwd_tw_offset(p);
     if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
     tw = p.rows_tw_smem ? tws : p.tw_rho;
-    sample_row_forward(p, m, jj, reinterpret_cast<float*>(bufA), anc, reinterpret_cast<float2*>(anc + p.r * p.n_eanc));
+    sample_row_forward(p, b, m, jj, reinterpret_cast<float*>(bufA), anc, reinterpret_cast<float2*>(anc + p.r * p.n_eanc));
   }
   __syncthreads();
   const float2* Z = fft_block<false>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
-  float2* out = p.xspec + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch;
+  float2* out = p.xspec + b * p.bs_x + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch;
   for (int k = threadIdx.x; k <= nc; k += blockDim.x) {
     const float2 zk = Z[k == nc ? 0 : k];
     const float2 zc = cconj(Z[k == 0 ? 0 : nc - k]);
@@ -447,8 +453,8 @@ __global__ void __launch_bounds__(kThreads) k_columns(DevPlan p, const float2* _
   float2* B = smem + G * nt;
   float2* tw = smem + 2 * G * nt;
   stage_table(tw, p.tw_th, nt, threadIdx.x, blockDim.x);
-  const int m = blockIdx.y, kr0 = blockIdx.x * G;
-  const float2* xin = p.xspec + static_cast<size_t>(m) * nh * p.x_pitch;
+  const int m = blockIdx.y, kr0 = blockIdx.x * G, b = blockIdx.z;
+  const float2* xin = p.xspec + b * p.bs_x + static_cast<size_t>(m) * nh * p.x_pitch;
   for (int idx = threadIdx.x; idx < G * nt; idx += blockDim.x) {
     const int g = idx % G, j = idx / G;
     const int jj = j - nh / 2;
@@ -470,7 +476,7 @@ __global__ void __launch_bounds__(kThreads) k_columns(DevPlan p, const float2* _
   }
   __syncthreads();
   const float2* Y = fft_block<true>(S, T, G, nt, p.rad_th, tw, threadIdx.x, blockDim.x);
-  float2* yout = p.yspec + static_cast<size_t>(m) * (nh + kHaloLo + kHaloHi) * p.x_pitch;
+  float2* yout = p.yspec + b * p.bs_ys + static_cast<size_t>(m) * (nh + kHaloLo + kHaloHi) * p.x_pitch;
   const int nrow = nh + kHaloLo + kHaloHi;
   for (int idx = threadIdx.x; idx < G * nrow; idx += blockDim.x) {
     const int g = idx % G, jr = idx / G;
@@ -488,9 +494,9 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
   float2* tws = smem + 2 * nc;
   if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
   const float2* tw = p.rows_tw_smem ? tws : p.tw_rho;
-  const int row = blockIdx.x, m = blockIdx.y;
+  const int row = blockIdx.x, m = blockIdx.y, b = blockIdx.z;
   const int nrow = p.nh + kHaloLo + kHaloHi;
-  const float2* X = p.yspec + (static_cast<size_t>(m) * nrow + row) * p.x_pitch;
+  const float2* X = p.yspec + b * p.bs_ys + (static_cast<size_t>(m) * nrow + row) * p.x_pitch;
   for (int k = threadIdx.x; k < nc; k += blockDim.x) {
     const float2 xk = X[k];
     const float2 xc = cconj(X[nc - k]);
@@ -501,8 +507,8 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
   __syncthreads();
   const float2* Z = fft_block<true>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
   const float* h = reinterpret_cast<const float*>(Z);
-  float* y = p.ylp + (static_cast<size_t>(m) * nrow + row) * p.y_pitch;
-  const int yrow = m * nrow + row;
+  float* y = p.ylp + b * p.bs_y + (static_cast<size_t>(m) * nrow + row) * p.y_pitch;
+  const int yrow = (b * p.M + m) * nrow + row;
   for (int c = static_cast<int>(threadIdx.x) - kPad; c < nr + kPad; c += blockDim.x) {
     int src = c < 0 ? c + nr : (c >= nr ? c - nr : c);
     if (p.use_tex)
@@ -518,15 +524,16 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
 // Interpolant of partition m's log-polar coefficients at (halo row It + at, padded column
 // Ir + ar); taps are clamped into the array.  With use_tex the coefficients are read with
 // tex2Dgather from the CUDA array (partition m occupies rows [m nrow, (m+1) nrow)).
-__device__ __forceinline__ float sample_lp(const DevPlan& p, int m, int It, float at, int Ir, float ar) {
+__device__ __forceinline__ float sample_lp(const DevPlan& p, int b, int m, int It, float at, int Ir, float ar) {
   const int nrow = p.nh + kHaloLo + kHaloHi;
+  const int pm = b * p.M + m;  // partition block in the (slice, partition)-stacked texture
   if (p.use_tex) {
     const cudaTextureObject_t t = p.tex_lp;
     if (p.interp == 3) {
       float wt[4], wr[4];
       bspline_w(at, wt);
       bspline_w(ar, wr);
-      const float y0 = static_cast<float>(m * nrow + clampi(It - 1, 0, nrow - 4)) + 1.f, y1 = y0 + 2.f;
+      const float y0 = static_cast<float>(pm * nrow + clampi(It - 1, 0, nrow - 4)) + 1.f, y1 = y0 + 2.f;
       const float x0 = static_cast<float>(clampi(Ir - 1, 0, p.y_pitch - 4)) + 1.f, x1 = x0 + 2.f;
       const float4 g00 = tex2Dgather<float4>(t, x0, y0, 0);
       const float4 g10 = tex2Dgather<float4>(t, x1, y0, 0);
@@ -539,12 +546,12 @@ __device__ __forceinline__ float sample_lp(const DevPlan& p, int m, int It, floa
       return fmaf(wt[0], r0, fmaf(wt[1], r1, fmaf(wt[2], r2, wt[3] * r3)));
     }
     const float4 g = tex2Dgather<float4>(t, static_cast<float>(clampi(Ir, 0, p.y_pitch - 2)) + 1.f,
-                                         static_cast<float>(m * nrow + clampi(It, 0, nrow - 2)) + 1.f, 0);
+                                         static_cast<float>(pm * nrow + clampi(It, 0, nrow - 2)) + 1.f, 0);
     const float v0 = fmaf(ar, g.z - g.w, g.w);
     const float v1 = fmaf(ar, g.y - g.x, g.x);
     return fmaf(at, v1 - v0, v0);
   }
-  const float* __restrict__ y = p.ylp + static_cast<size_t>(m) * nrow * p.y_pitch;
+  const float* __restrict__ y = p.ylp + b * p.bs_y + static_cast<size_t>(m) * nrow * p.y_pitch;
   if (p.interp == 3) {
     float wt[4], wr[4];
     bspline_w(at, wt);
@@ -571,8 +578,9 @@ __device__ __forceinline__ float sample_lp(const DevPlan& p, int m, int It, floa
 
 // R f(theta_a, s_k) = a_R^{-1} * interpolant of partition m at S_m(theta_a, s_k).
 __global__ void __launch_bounds__(128) k_gather_sino(DevPlan p, float* __restrict__ sino) {
-  const int a = blockIdx.y;
+  const int a = blockIdx.y, b = blockIdx.z;
   const int k = blockIdx.x * 128 + threadIdx.x;
+  sino += static_cast<size_t>(b) * p.n_angles * p.n_det;
   const int nd = p.n_det;
   if (k >= nd) return;
   float out = 0.f;
@@ -582,7 +590,7 @@ __global__ void __launch_bounds__(128) k_gather_sino(DevPlan p, float* __restric
     const int n = k - (k / kKTile) * kKTile;
     const float cr = fmaf(log1pf(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
     const float fr = floorf(cr);
-    out = sample_lp(p, ang.x, ang.z, __int_as_float(ang.w), anc.x + static_cast<int>(fr), cr - fr) * p.inv_aR;
+    out = sample_lp(p, b, ang.x, ang.z, __int_as_float(ang.w), anc.x + static_cast<int>(fr), cr - fr) * p.inv_aR;
   }
   sino[static_cast<size_t>(a) * nd + k] = out;
 }
@@ -590,7 +598,8 @@ __global__ void __launch_bounds__(128) k_gather_sino(DevPlan p, float* __restric
 // R# g(x) = sum_m interpolant of partition m at the log-polar coordinates of T_m x.
 __global__ void __launch_bounds__(kPTile * kPTile) k_gather_image(DevPlan p, float* __restrict__ img) {
   const int N = p.N;
-  const int tj = blockIdx.x, ti = blockIdx.y;
+  const int tj = blockIdx.x, ti = blockIdx.y, b = blockIdx.z;
+  img += static_cast<size_t>(b) * N * N;
   const int j = tj * kPTile + threadIdx.x, i = ti * kPTile + threadIdx.y;
   if (i >= N || j >= N) return;
   float acc = 0.f;
@@ -613,7 +622,7 @@ __global__ void __launch_bounds__(kPTile * kPTile) k_gather_image(DevPlan p, flo
       const float ct = fmaf(dth, p.inv_dphi, __int_as_float(a0.y));
       const float cr = fmaf(drho, p.inv_drho, __int_as_float(a0.w));
       const float ft = floorf(ct), fr = floorf(cr);
-      acc += sample_lp(p, m, a0.x + static_cast<int>(ft), ct - ft, a0.z + static_cast<int>(fr), cr - fr);
+      acc += sample_lp(p, b, m, a0.x + static_cast<int>(ft), ct - ft, a0.z + static_cast<int>(fr), cr - fr);
     }
   }
   img[static_cast<size_t>(i) * N + j] = acc;
@@ -683,11 +692,11 @@ size_t rows_fwd_smem(const DevPlan& p) {
 size_t cols_smem(const DevPlan& p) { return (2 * static_cast<size_t>(p.col_group) + 1) * p.n_theta * sizeof(float2); }
 
 void launch_columns_and_inverse(const DevPlan& p, const float2* kern, cudaStream_t st, const StageHook& hook,
-                                int stage0) {
+                                int stage0, int batch) {
   const int ngroups = (p.nc + 1 + p.col_group - 1) / p.col_group;
-  k_columns<<<dim3(ngroups, p.M), kThreads, cols_smem(p), st>>>(p, kern);
+  k_columns<<<dim3(ngroups, p.M, batch), kThreads, cols_smem(p), st>>>(p, kern);
   hook(stage0, st);
-  k_rows_inv<<<dim3(p.nh + kHaloLo + kHaloHi, p.M), kThreads, rows_smem(p), st>>>(p);
+  k_rows_inv<<<dim3(p.nh + kHaloLo + kHaloHi, p.M, batch), kThreads, rows_smem(p), st>>>(p);
   hook(stage0 + 1, st);
 }
 
@@ -716,30 +725,36 @@ cudaError_t configure_kernels(DevPlan& p) {
   return cudaSuccess;
 }
 
-cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cudaStream_t st, StageHook hook) {
+cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cudaStream_t st, StageHook hook,
+                           int batch) {
+  if (batch < 1 || batch > p.batch_cap) return cudaErrorInvalidValue;
   hook(-1, st);
   ImageSource isrc{image, p.N};
-  k_prefilter<ImageSource><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows), kThreads, 0, st>>>(
-      p, isrc, p.N, p.N, p.use_tex ? nullptr : p.coef_img, p.img_pitch, kPad, p.use_tex ? p.surf_img : 0);
+  k_prefilter<ImageSource><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows, batch), kThreads, 0, st>>>(
+      p, isrc, p.N, p.N, p.use_tex ? nullptr : p.coef_img, p.img_pitch, kPad, p.bs_img, p.use_tex ? p.surf_img : 0,
+      p.tex_img_rows);
   hook(0, st);
-  k_rows_fwd<false><<<dim3(p.nh, p.M), kThreads, rows_fwd_smem(p), st>>>(p);
+  k_rows_fwd<false><<<dim3(p.nh, p.M, batch), kThreads, rows_fwd_smem(p), st>>>(p);
   hook(1, st);
-  launch_columns_and_inverse(p, p.k_fwd, st, hook, 2);
-  k_gather_sino<<<dim3((p.n_det + 127) / 128, p.n_angles), 128, 0, st>>>(p, sino);
+  launch_columns_and_inverse(p, p.k_fwd, st, hook, 2, batch);
+  k_gather_sino<<<dim3((p.n_det + 127) / 128, p.n_angles, batch), 128, 0, st>>>(p, sino);
   hook(4, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook) {
+cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook,
+                               int batch) {
+  if (batch < 1 || batch > p.batch_cap) return cudaErrorInvalidValue;
   hook(-1, st);
   SinoSource ssrc{sino, p.n_angles, p.n_det, p.live_lo, p.live_hi};
-  k_prefilter<SinoSource><<<dim3((p.n_det + 1 + kPfCols - 1) / kPfCols, (p.n_angles + kPfRows - 1) / kPfRows), kThreads, 0,
-                            st>>>(p, ssrc, p.n_angles, p.n_det + 1, p.coef_sino, p.sino_pitch, 0, 0);
+  k_prefilter<SinoSource><<<dim3((p.n_det + 1 + kPfCols - 1) / kPfCols, (p.n_angles + kPfRows - 1) / kPfRows, batch),
+                            kThreads, 0, st>>>(p, ssrc, p.n_angles, p.n_det + 1, p.coef_sino, p.sino_pitch, 0, p.bs_sino, 0,
+                                               0);
   hook(5, st);
-  k_rows_fwd<true><<<dim3(p.nh, p.M), kThreads, rows_smem(p), st>>>(p);
+  k_rows_fwd<true><<<dim3(p.nh, p.M, batch), kThreads, rows_smem(p), st>>>(p);
   hook(6, st);
-  launch_columns_and_inverse(p, p.k_bp, st, hook, 7);
-  k_gather_image<<<dim3(p.n_ptiles, p.n_ptiles), dim3(kPTile, kPTile), 0, st>>>(p, image);
+  launch_columns_and_inverse(p, p.k_bp, st, hook, 7, batch);
+  k_gather_image<<<dim3(p.n_ptiles, p.n_ptiles, batch), dim3(kPTile, kPTile), 0, st>>>(p, image);
   hook(9, st);
   return cudaGetLastError();
 }

@@ -54,6 +54,10 @@ struct DevPlan {
   float2* yspec;       // M x (nh + 4) x x_pitch
   float* ylp;          // M x (nh + 4) x y_pitch
   float* sino_tmp;     // n_angles x n_det (filtered sinogram for FBP)
+  // batches of same-size slices: slice b = blockIdx.z uses scratch at these strides (elements)
+  size_t bs_img, bs_sino, bs_x, bs_ys, bs_y;
+  int tex_img_rows;    // rows per slice in the image texture: N data rows + kTexGap zero rows
+  int batch_cap;       // slices the scratch and the textures hold
   int n_filt;          // FBP: zero-padded real FFT length along s
   int filt_tw_smem;    // 1: the FBP row kernel stages its twiddles in shared memory
   RadixList rad_filt;
@@ -71,9 +75,14 @@ struct StageHook {
   }
 };
 
-// Each returns cudaGetLastError() after its launches.
-cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cudaStream_t st, StageHook hook);
-cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook);
+constexpr int kTexGap = 3;  // zero rows after each slice of the image texture (cubic taps reach 3 rows)
+
+// Each returns cudaGetLastError() after its launches.  `batch` same-size slices (contiguous
+// [batch][...] inputs and outputs, batch <= p.batch_cap) are processed by the same launches.
+cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cudaStream_t st, StageHook hook,
+                           int batch = 1);
+cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook,
+                               int batch = 1);
 cudaError_t launch_fbp(const DevPlan& p, const float* sino, float* image, int filter, cudaStream_t st, StageHook hook);
 
 // Dynamic shared memory limits are raised once per device.

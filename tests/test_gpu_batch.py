@@ -1,0 +1,95 @@
+"""Batched slices: same-size batches in one set of launches, uneven sizes grouped, CUDA graph."""
+
+import numpy as np
+import pytest
+
+from workloads import ellipse_image, random_ellipses, random_sinogram
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rl():
+    from paper_1506_00014_gb300 import build
+
+    if build.needs_build():
+        build.build()
+    import paper_1506_00014_gb300 as rl
+
+    return rl
+
+
+def _t(a):
+    return torch.tensor(np.asarray(a, np.float32), device="cuda")
+
+
+@pytest.mark.parametrize("N,na,nd,interp", [(128, 128, 192, 3), (96, 100, 150, 1)])
+def test_same_size_batch_equals_single_calls(rl, N, na, nd, interp):
+    plan = rl.radon_plan_create(N, na, nd, interp, 3)
+    rl.radon_plan_reserve_batch(plan, 4)
+    imgs = torch.stack([_t(ellipse_image(N, random_ellipses(8, s))) for s in range(3)]).contiguous()
+    sins = torch.stack([_t(random_sinogram(na, nd, 10 + s)) for s in range(3)]).contiguous()
+    out_s = torch.empty((3, na, nd), device="cuda")
+    out_i = torch.empty((3, N, N), device="cuda")
+    rl.radon_forward_batch(plan, imgs, out_s)
+    rl.radon_backproject_batch(plan, sins, out_i)
+    for b in range(3):
+        one_s = torch.empty((na, nd), device="cuda")
+        one_i = torch.empty((N, N), device="cuda")
+        rl.radon_forward(plan, imgs[b].contiguous(), one_s)
+        rl.radon_backproject(plan, sins[b].contiguous(), one_i)
+        assert torch.equal(out_s[b], one_s)
+        assert torch.equal(out_i[b], one_i)
+
+
+def test_batch_capacity_limits(rl):
+    plan = rl.radon_plan_create(64, 64, 96, 3, 3)
+    x = torch.zeros((2, 64, 64), device="cuda")
+    y = torch.zeros((2, 64, 96), device="cuda")
+    with pytest.raises(rl.RadonError):  # capacity is 1 until reserved
+        rl.radon_forward_batch(plan, x, y)
+    big = rl.radon_plan_create(4096, 4096, 6144, 3, 3)
+    with pytest.raises(rl.RadonError) as err:  # 20 x 4099 texture rows exceed the surface height
+        rl.radon_plan_reserve_batch(big, 20)
+    assert err.value.status == 5  # RADON_NOT_SUPPORTED
+    with pytest.raises(rl.RadonError) as err:  # so few angles at this size need too many sub-angles
+        rl.radon_plan_create(4096, 64, 96, 3, 3)
+    assert err.value.status == 5
+
+
+def test_column_group_does_not_change_results(rl):
+    N = 128
+    plan = rl.radon_plan_create(N, N, 192, 3, 3)
+    f = _t(ellipse_image(N, random_ellipses(10, 1)))
+    outs = []
+    for g in (1, 2, 4):
+        rl.radon_plan_set_column_group(plan, g)
+        s = torch.empty((N, 192), device="cuda")
+        rl.radon_forward(plan, f, s)
+        outs.append(s)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_uneven_batch_with_graph_matches_per_slice(rl):
+    from paper_1506_00014_gb300.batch import UnevenBatch
+
+    sizes = [64, 128, 64, 96, 128, 64]
+    ub = UnevenBatch(sizes, max_batch=2)
+    choice = ub.tune()
+    assert set(choice) == {64, 96, 128}
+    imgs = [_t(ellipse_image(n, random_ellipses(6, 40 + i))) for i, n in enumerate(sizes)]
+    ub.set_images(imgs)
+    ub.forward()
+    eager = [ub.sinogram(i).clone() for i in range(len(sizes))]
+    for i, n in enumerate(sizes):
+        plan = ub.plans[n]
+        one = torch.empty(plan.sino_shape, device="cuda")
+        rl.radon_forward(plan, imgs[i], one)
+        assert torch.equal(one, eager[i])
+    ub.capture(lambda: ub.forward())
+    ub.set_images(imgs)
+    ub.replay()
+    torch.cuda.synchronize()
+    for i in range(len(sizes)):
+        assert torch.equal(ub.sinogram(i), eager[i])
