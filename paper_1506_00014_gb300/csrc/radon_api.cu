@@ -103,16 +103,13 @@ radon::StageHook hook_of(radon_plan_s* p) {
 // Frees the scratch buffer and the texture storage (the device must be idle).
 void release_scratch(radon_plan_s* p) {
   radon::DevPlan& d = p->dp;
-  if (d.tex_img) cudaDestroyTextureObject(d.tex_img);
-  if (d.surf_img) cudaDestroySurfaceObject(d.surf_img);
   if (d.tex_lp) cudaDestroyTextureObject(d.tex_lp);
   if (d.surf_lp) cudaDestroySurfaceObject(d.surf_lp);
-  if (p->img_array) cudaFreeArray(p->img_array);
   if (p->lp_array) cudaFreeArray(p->lp_array);
   if (p->scratch_mem) cudaFree(p->scratch_mem);
-  d.tex_img = d.tex_lp = 0;
-  d.surf_img = d.surf_lp = 0;
-  p->img_array = p->lp_array = nullptr;
+  d.tex_lp = 0;
+  d.surf_lp = 0;
+  p->lp_array = nullptr;
   p->scratch_mem = nullptr;
 }
 
@@ -138,8 +135,8 @@ cudaError_t make_texture(int width, int height, cudaArray_t* arr, cudaTextureObj
 }
 
 // Scratch buffers and texture storage for `cap` same-size slices; replaces the previous ones.
-// Slice b of a batch uses the buffers at offset b * (per-slice size); its image-texture rows are
-// [b (N + kTexGap), b (N + kTexGap) + N) with kTexGap zero rows after them.
+// Slice b of a batch uses the buffers at offset b * (per-slice size) and the log-polar texture
+// rows [b M nrow, (b + 1) M nrow).
 cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
   radon::DevPlan& d = p->dp;
   const int N = d.N, na = d.n_angles, nd = d.n_det;
@@ -149,14 +146,12 @@ cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
   const size_t e_x = static_cast<size_t>(d.M) * d.nh * d.x_pitch;
   const size_t e_ys = static_cast<size_t>(d.M) * nrow * d.x_pitch;
   const size_t e_y = static_cast<size_t>(d.M) * nrow * d.y_pitch;
-  const int img_rows = N + radon::kTexGap;
-  const long long tex_img_h = static_cast<long long>(cap) * img_rows;
   const long long tex_lp_h = static_cast<long long>(cap) * d.M * static_cast<long long>(nrow);
   int dev = 0, max_h = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxSurface2DHeight, dev);
   if (e != cudaSuccess) return e;
-  if (cap < 1 || tex_img_h > max_h || tex_lp_h > max_h) return cudaErrorInvalidValue;
+  if (cap < 1 || tex_lp_h > max_h) return cudaErrorInvalidValue;
   size_t sc = 0;
   auto take = [&](size_t bytes) {
     const size_t off = sc;
@@ -164,6 +159,7 @@ cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
     return off;
   };
   const size_t s_img = take(sizeof(float) * e_img * cap);
+  const size_t s_q4 = take(sizeof(float4) * e_img * cap);
   const size_t s_sino = take(sizeof(float) * e_sino * cap);
   const size_t s_x = take(sizeof(float2) * e_x * cap);
   const size_t s_ys = take(sizeof(float2) * e_ys * cap);
@@ -172,25 +168,19 @@ cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
   const size_t s_io_img = take(sizeof(float) * static_cast<size_t>(N) * N);
   const size_t s_io_sino = take(sizeof(float) * static_cast<size_t>(na) * nd);
   void* mem = nullptr;
-  cudaArray_t img_arr = nullptr, lp_arr = nullptr;
-  cudaTextureObject_t tex_img = 0, tex_lp = 0;
-  cudaSurfaceObject_t surf_img = 0, surf_lp = 0;
+  cudaArray_t lp_arr = nullptr;
+  cudaTextureObject_t tex_lp = 0;
+  cudaSurfaceObject_t surf_lp = 0;
   e = cudaMalloc(&mem, sc);
   if (e == cudaSuccess) e = cudaMemset(mem, 0, sc);
-  if (e == cudaSuccess) e = make_texture(N, static_cast<int>(tex_img_h), &img_arr, &tex_img, &surf_img);
   if (e == cudaSuccess) e = make_texture(d.y_pitch, static_cast<int>(tex_lp_h), &lp_arr, &tex_lp, &surf_lp);
-  // the arrays start undefined: copy zeros (the fresh scratch) into them
-  if (e == cudaSuccess)
-    e = cudaMemcpy2DToArray(img_arr, 0, 0, mem, sizeof(float) * N, sizeof(float) * N, tex_img_h, cudaMemcpyDeviceToDevice);
+  // the array starts undefined: copy zeros (the fresh scratch) into it
   if (e == cudaSuccess)
     e = cudaMemcpy2DToArray(lp_arr, 0, 0, static_cast<char*>(mem) + s_y, sizeof(float) * d.y_pitch,
                             sizeof(float) * d.y_pitch, tex_lp_h, cudaMemcpyDeviceToDevice);
   if (e != cudaSuccess) {
-    if (tex_img) cudaDestroyTextureObject(tex_img);
-    if (surf_img) cudaDestroySurfaceObject(surf_img);
     if (tex_lp) cudaDestroyTextureObject(tex_lp);
     if (surf_lp) cudaDestroySurfaceObject(surf_lp);
-    if (img_arr) cudaFreeArray(img_arr);
     if (lp_arr) cudaFreeArray(lp_arr);
     cudaFree(mem);
     return e;
@@ -198,14 +188,13 @@ cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
   release_scratch(p);
   char* sb = static_cast<char*>(mem);
   p->scratch_mem = mem;
-  p->img_array = img_arr;
   p->lp_array = lp_arr;
-  d.tex_img = tex_img;
-  d.surf_img = surf_img;
   d.tex_lp = tex_lp;
   d.surf_lp = surf_lp;
   d.use_tex = 1;
   d.coef_img = reinterpret_cast<float*>(sb + s_img);
+  d.coef_q4 = reinterpret_cast<float4*>(sb + s_q4);
+  d.img_quad = 1;
   d.coef_sino = reinterpret_cast<float*>(sb + s_sino);
   d.xspec = reinterpret_cast<float2*>(sb + s_x);
   d.yspec = reinterpret_cast<float2*>(sb + s_ys);
@@ -216,12 +205,10 @@ cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
   d.bs_x = e_x;
   d.bs_ys = e_ys;
   d.bs_y = e_y;
-  d.tex_img_rows = img_rows;
   d.batch_cap = cap;
   p->io_image = reinterpret_cast<float*>(sb + s_io_img);
   p->io_sino = reinterpret_cast<float*>(sb + s_io_sino);
-  p->info.device_bytes = p->table_bytes + sc + sizeof(float) * (static_cast<size_t>(N) * tex_img_h +
-                                                                 static_cast<size_t>(d.y_pitch) * tex_lp_h);
+  p->info.device_bytes = p->table_bytes + sc + sizeof(float) * static_cast<size_t>(d.y_pitch) * tex_lp_h;
   return cudaSuccess;
 }
 

@@ -26,6 +26,7 @@ namespace radon {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kDiscMargin = 16;  // pixels beyond the unit disc still sampled by the forward rows
 
 __device__ __forceinline__ int odd_ext(int p, int n, float* sgn) {
   // extension of [0, n) that is odd about -1 and about n (period 2n + 2)
@@ -270,10 +271,10 @@ __device__ __forceinline__ float sample_image(const DevPlan& p, int b, int ic, f
 // shared memory as (integer, fraction); each sample adds the FP32 offset (e^rho_i - e^rho_anchor)
 // times the direction.
 //
-// Taps: with use_tex the 4 x 4 window comes from four tex2Dgather fetches of the coefficient
-// image held in a CUDA array (block-linear, so rays in every direction stay cache-friendly);
-// each fetch is centred on an integer texel corner, so it returns four stored values exactly
-// (no filtering).  Otherwise the taps are plain global loads from the padded coefficient image.
+// Taps: with img_quad each of the 4 tap rows is one aligned 16-byte load from the quad layout;
+// otherwise 16 scalar loads from the padded coefficient image.  Samples more than kDiscMargin
+// pixels outside the unit disc are skipped: the pre-filtered disc-masked image decays like
+// 0.27^d away from the disc, below 1e-8 of its maximum there.
 
 // Shared-memory layout of a forward row CTA (float2 units): bufA, bufB (nc each), the 16-byte
 // aligned anchor table (float4 per sub-angle and tile), the sub-angle directions, the twiddles.
@@ -282,29 +283,33 @@ __host__ __device__ __forceinline__ int fwd_tw_offset(const DevPlan& p) {
   return fwd_anchor_offset(p) + 2 * p.r * p.n_eanc + p.r + 1;
 }
 
-// Interpolant from the texture at unpadded index coordinates (ic + ac, ir + ar).
-__device__ __forceinline__ float sample_image_tex(cudaTextureObject_t tex, int ic, float ac, int ir, float ar, bool cubic) {
-  if (cubic) {
-    float wc[4], wr[4];
-    bspline_w(ac, wc);
-    bspline_w(ar, wr);
-    // gather at (x0 + 1, y0 + 1) returns texels (x0, y1), (x0+1, y1), (x0+1, y0), (x0, y0) in .x .y .z .w
-    const float x0 = static_cast<float>(ic - 1) + 1.f, x1 = x0 + 2.f;
-    const float y0 = static_cast<float>(ir - 1) + 1.f, y1 = y0 + 2.f;
-    const float4 g00 = tex2Dgather<float4>(tex, x0, y0, 0);  // rows ir-1, ir   cols ic-1, ic
-    const float4 g10 = tex2Dgather<float4>(tex, x1, y0, 0);  // rows ir-1, ir   cols ic+1, ic+2
-    const float4 g01 = tex2Dgather<float4>(tex, x0, y1, 0);  // rows ir+1, ir+2 cols ic-1, ic
-    const float4 g11 = tex2Dgather<float4>(tex, x1, y1, 0);  // rows ir+1, ir+2 cols ic+1, ic+2
-    const float r0 = fmaf(wc[0], g00.w, fmaf(wc[1], g00.z, fmaf(wc[2], g10.w, wc[3] * g10.z)));
-    const float r1 = fmaf(wc[0], g00.x, fmaf(wc[1], g00.y, fmaf(wc[2], g10.x, wc[3] * g10.y)));
-    const float r2 = fmaf(wc[0], g01.w, fmaf(wc[1], g01.z, fmaf(wc[2], g11.w, wc[3] * g11.z)));
-    const float r3 = fmaf(wc[0], g01.x, fmaf(wc[1], g01.y, fmaf(wc[2], g11.x, wc[3] * g11.y)));
-    return fmaf(wr[0], r0, fmaf(wr[1], r1, fmaf(wr[2], r2, wr[3] * r3)));
+// Interpolant from the quad layout at padded index coordinates (ic + ac, ir + ar): one 16-byte
+// load per tap row.
+__device__ __forceinline__ float sample_image_quad(const DevPlan& p, int b, int ic, float ac, int ir, float ar) {
+  const float4* __restrict__ base = p.coef_q4 + b * p.bs_img + static_cast<size_t>(ir - 1) * p.img_pitch + (ic - 1);
+  float wc[4], wr[4];
+  bspline_w(ac, wc);
+  bspline_w(ar, wr);
+  float acc = 0.f;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const float4 v = __ldg(base + d * p.img_pitch);
+    acc = fmaf(wr[d], fmaf(wc[0], v.x, fmaf(wc[1], v.y, fmaf(wc[2], v.z, wc[3] * v.w))), acc);
   }
-  const float4 g = tex2Dgather<float4>(tex, static_cast<float>(ic) + 1.f, static_cast<float>(ir) + 1.f, 0);
-  const float v0 = fmaf(ac, g.z - g.w, g.w);  // row ir
-  const float v1 = fmaf(ac, g.y - g.x, g.x);  // row ir + 1
-  return fmaf(ar, v1 - v0, v0);
+  return acc;
+}
+
+// Expands the padded coefficient image into the quad layout (one slice per blockIdx.z).
+__global__ void __launch_bounds__(kThreads) k_quad(DevPlan p) {
+  const int P = p.img_pitch, b = blockIdx.z;
+  const float* __restrict__ src = p.coef_img + b * p.bs_img;
+  float4* __restrict__ dst = p.coef_q4 + b * p.bs_img;
+  const int r = blockIdx.y;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P; c += gridDim.x * blockDim.x) {
+    const float* q = src + static_cast<size_t>(r) * P + c;
+    dst[static_cast<size_t>(r) * P + c] =
+        make_float4(q[0], c + 1 < P ? q[1] : 0.f, c + 2 < P ? q[2] : 0.f, c + 3 < P ? q[3] : 0.f);
+  }
 }
 
 __device__ void sample_row_forward(const DevPlan& p, int b, int m, int jj, float* __restrict__ h,
@@ -326,7 +331,8 @@ __device__ void sample_row_forward(const DevPlan& p, int b, int m, int jj, float
     if (tile == 0) dir[q] = make_float2(cs.x, cs.z);
   }
   __syncthreads();
-  const int P = p.img_pitch;
+  const int P = p.img_pitch, half = p.N / 2;
+  const unsigned reach2 = static_cast<unsigned>((half + kDiscMargin) * (half + kDiscMargin));
   for (int tile = warp; tile < ne; tile += nw) {
     const int i = tile * kETile + lane;
     const bool valid = i < p.N_rho;
@@ -340,8 +346,10 @@ __device__ void sample_row_forward(const DevPlan& p, int b, int m, int jj, float
       const float fc = floorf(Fc), fr = floorf(Fr);
       const int ic = static_cast<int>(a.x + fc), ir = static_cast<int>(a.z + fr);  // padded indices
       if (ic < 1 || ic > P - 3 || ir < 1 || ir > P - 3) continue;                 // every tap is zero
-      acc += p.use_tex ? sample_image_tex(p.tex_img, ic - kPad, Fc - fc, ir - kPad + b * p.tex_img_rows, Fr - fr, cubic)
-                       : sample_image(p, b, ic, Fc - fc, ir, Fr - fr);
+      const int dx = ic - kPad - half, dy = ir - kPad - half;
+      if (static_cast<unsigned>(dx * dx) + static_cast<unsigned>(dy * dy) > reach2) continue;
+      acc += (p.img_quad && cubic) ? sample_image_quad(p, b, ic, Fc - fc, ir, Fr - fr)
+                                   : sample_image(p, b, ic, Fc - fc, ir, Fr - fr);
     }
     if (valid) h[i] = acc * e.x;
   }
@@ -731,8 +739,9 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
   hook(-1, st);
   ImageSource isrc{image, p.N};
   k_prefilter<ImageSource><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows, batch), kThreads, 0, st>>>(
-      p, isrc, p.N, p.N, p.use_tex ? nullptr : p.coef_img, p.img_pitch, kPad, p.bs_img, p.use_tex ? p.surf_img : 0,
-      p.tex_img_rows);
+      p, isrc, p.N, p.N, p.coef_img, p.img_pitch, kPad, p.bs_img, 0, 0);
+  if (p.img_quad && p.interp == 3)
+    k_quad<<<dim3((p.img_pitch + kThreads - 1) / kThreads, p.img_pitch, batch), kThreads, 0, st>>>(p);
   hook(0, st);
   k_rows_fwd<false><<<dim3(p.nh, p.M, batch), kThreads, rows_fwd_smem(p), st>>>(p);
   hook(1, st);

@@ -43,9 +43,9 @@ struct DevPlan {
   const float* filt;   // FBP transfer functions / n_filt: 3 tables of n_filt/2 + 1 real bins
   // scratch
   float* coef_img;     // (N + 2 kPad)^2, zero border
-  int use_tex;         // 1: the forward sampling reads the coefficient image through tex_img
-  cudaTextureObject_t tex_img;   // N x N CUDA array holding Q f (border mode: zero outside)
-  cudaSurfaceObject_t surf_img;  // write view of the same array (filled by the pre-filter)
+  float4* coef_q4;     // same grid; element (r, c) holds coefficients (r, c .. c+3) (zero past the edge)
+  int img_quad;        // 1: forward sampling reads coef_q4 (one 16-byte load per tap row)
+  int use_tex;         // 1: the log-polar coefficients are read through tex_lp
   cudaTextureObject_t tex_lp;    // log-polar coefficients, M (nh + 4) rows x y_pitch columns
   cudaSurfaceObject_t surf_lp;   // write view (filled by the inverse rho FFT)
   int rows_tw_smem;    // 1: row kernels stage the rho twiddles in shared memory
@@ -56,7 +56,6 @@ struct DevPlan {
   float* sino_tmp;     // n_angles x n_det (filtered sinogram for FBP)
   // batches of same-size slices: slice b = blockIdx.z uses scratch at these strides (elements)
   size_t bs_img, bs_sino, bs_x, bs_ys, bs_y;
-  int tex_img_rows;    // rows per slice in the image texture: N data rows + kTexGap zero rows
   int batch_cap;       // slices the scratch and the textures hold
   int n_filt;          // FBP: zero-padded real FFT length along s
   int filt_tw_smem;    // 1: the FBP row kernel stages its twiddles in shared memory
@@ -74,8 +73,6 @@ struct StageHook {
     if (mark) mark(ctx, stage, st);
   }
 };
-
-constexpr int kTexGap = 3;  // zero rows after each slice of the image texture (cubic taps reach 3 rows)
 
 // Each returns cudaGetLastError() after its launches.  `batch` same-size slices (contiguous
 // [batch][...] inputs and outputs, batch <= p.batch_cap) are processed by the same launches.
