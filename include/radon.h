@@ -64,7 +64,7 @@ typedef struct {
   int r;              /* fine angular sub-samples per coarse angle (Omega_lp -> Omega_p)       */
   int n_quad;         /* trapezoid nodes used for the kernel integrals (Eq. weightsa)          */
   int n_filter;       /* zero-padded FFT length of the FBP filter along s (>= 2 n_det)          */
-  int column_group;   /* rho frequencies per CTA of the theta convolution (performance knob)    */
+  int column_group;   /* theta convolution kernel: 0 specialised, else rho frequencies per CTA */
   double beta, a_R, a_r, L;       /* pi/M, Eq. aconst, L = -log(a_r)                           */
   double d_phi, d_rho, d_s, d_theta;
   size_t device_bytes;            /* device memory owned by the plan (tables + scratch)        */
@@ -112,8 +112,12 @@ int radon_plan_reserve_batch(radon_plan plan, int max_batch);
 int radon_forward_batch(radon_plan plan, const float* d_images, float* d_sinos, int batch, void* stream);
 int radon_backproject_batch(radon_plan plan, const float* d_sinos, float* d_images, int batch, void* stream);
 
-/* Number of rho frequencies (1, 2 or 4) one CTA of the theta convolution transforms.  A pure
- * performance knob (results are unchanged); RADON_NOT_SUPPORTED if the value does not fit. */
+/* Kernel of the theta convolution (the column FFTs of Sections 3 and 5), a performance knob.
+ * group 0: the specialised in-place kernel, available when n_theta is a power of two from 256
+ * to 8192 (the default there); group 1, 2 or 4: the generic mixed-radix kernel with that many rho
+ * frequencies per CTA (the default otherwise).  Groups 1, 2 and 4 give identical results; group 0
+ * differs from them by FP32 rounding only.  RADON_NOT_SUPPORTED if the kernel is unavailable or
+ * does not fit. */
 int radon_plan_set_column_group(radon_plan plan, int group);
 
 /* Same as radon_forward / radon_backproject but with HOST buffers: the call copies the input to

@@ -88,7 +88,7 @@ class UnevenBatch:
         self.graph.replay()
 
     # ---------------------------------------------------------------- autotuning
-    def tune(self, groups=(1, 2, 4), repeats: int = 3):
+    def tune(self, groups=(0, 1, 2, 4), repeats: int = 3):
         """Choose each plan's column group by timing one batched R + R# (numerics unchanged).
         Uses (and overwrites) the group buffers: set the inputs afterwards."""
         choice = {}

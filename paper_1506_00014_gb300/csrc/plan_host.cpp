@@ -191,6 +191,12 @@ void kernel_quadrant(const radon_plan_info& g, int which, std::vector<double>* o
   });
 }
 
+int column_radices_index(int n_theta) {
+  for (int i = 0; i < kNumColumnRadices; ++i)
+    if (kColumnRadices[i].n == n_theta) return i;
+  return -1;
+}
+
 int build_tables(const radon_plan_info& g, HostTables* t) {
   const int N = g.N, na = g.n_angles, nd = g.n_det, M = g.n_partitions;
   const int nh = g.n_theta_half, nt = g.n_theta, nr = g.N_rho, nc = nr / 2, r = g.r;
@@ -207,6 +213,24 @@ int build_tables(const radon_plan_info& g, HostTables* t) {
   twiddles(nc, nc, &t->tw_rho);
   twiddles(nr, nc + 1, &t->tw_r2c);
   twiddles(nt, nt, &t->tw_th);
+  // Specialised column transform: pass after NS combined points with radix R reads
+  // exp(-2 pi i r k / (NS R)) at [k][r - 1]; the passes' tables are concatenated.
+  t->col_fixed = column_radices_index(nt);
+  t->tw_col.clear();
+  if (t->col_fixed >= 0) {
+    int ns = 1;
+    for (int i = 0; i < 4 && kColumnRadices[t->col_fixed].r[i] > 0; ++i) {
+      const int R = kColumnRadices[t->col_fixed].r[i];
+      if (ns > 1)
+        for (int k = 0; k < ns; ++k)
+          for (int q = 1; q < R; ++q) {
+            const double a = -2.0 * kPi * q * k / (static_cast<double>(ns) * R);
+            t->tw_col.push_back(static_cast<float>(std::cos(a)));
+            t->tw_col.push_back(static_cast<float>(std::sin(a)));
+          }
+      ns *= R;
+    }
+  }
 
   // Fourier multipliers (the convolution steps of Algorithms 1 and 2): zeta_hat / B_hat with the
   // inverse-DFT normalisation 1/(n_theta N_rho); the forward one also divided by the in-band

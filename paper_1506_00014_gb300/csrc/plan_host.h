@@ -22,6 +22,22 @@ constexpr int kHaloHi = 2;   // and above it (cubic taps of |phi| <= beta/2)
 constexpr int kPad = 3;      // zero border around the coefficient arrays (cubic taps never leave it)
 constexpr int kFirHalf = 14; // one-sided length of the truncated pre-filter (|z|^15 ~ 2.7e-9)
 
+// Column (theta) transform lengths with a specialised in-place kernel: G columns per work item,
+// TH threads per CTA, at least MINB resident CTAs per SM, and the radix sequence (0 ends it).
+struct ColumnRadices {
+  int n, G, TH, MINB;
+  int r[4];
+};
+constexpr ColumnRadices kColumnRadices[] = {
+    {256, 32, 256, 2, {16, 16, 0, 0}},  {512, 16, 256, 2, {8, 8, 8, 0}},     {1024, 8, 256, 2, {16, 8, 8, 0}},
+    {2048, 4, 256, 2, {16, 16, 8, 0}},  {4096, 2, 256, 2, {16, 16, 16, 0}}, {8192, 1, 256, 2, {16, 16, 16, 2}},
+    {1372, 4, 196, 2, {14, 14, 7, 0}},
+};
+constexpr int kNumColumnRadices = sizeof(kColumnRadices) / sizeof(kColumnRadices[0]);
+
+// Index into kColumnRadices, or -1 when n_theta has no specialised kernel.
+int column_radices_index(int n_theta);
+
 struct Radices {
   int n = 0;
   int count = 0;
@@ -43,6 +59,8 @@ struct HostTables {
   std::vector<float> tw_rho;   // 2 * (N_rho/2): exp(-2 pi i p / (N_rho/2))
   std::vector<float> tw_r2c;   // 2 * (N_rho/2 + 1): exp(-2 pi i k / N_rho)
   std::vector<float> tw_th;    // 2 * n_theta: exp(-2 pi i p / n_theta)
+  int col_fixed = -1;          // kColumnRadices index, -1: generic column kernel
+  std::vector<float> tw_col;   // per-pass twiddles of the specialised column transform
   std::vector<float> k_fwd;    // 2 * (N_rho/2+1) * (n_theta/2+1), [k_rho][k_theta]
   std::vector<float> k_bp;     // same layout, back-projection kernel
   // forward sampling (Algorithm 1: resample T_m f on Omega_lp, downsample, multiply by e^rho)

@@ -317,6 +317,7 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.inv_aR = static_cast<float>(1.0 / g.a_R);
   d.d_s = static_cast<float>(g.d_s);
   d.n_filt = g.n_filter;
+  d.col_fixed = t.col_fixed;
   if (!copy_radices(t.rad_rho, 1, &d.rad_rho) || !copy_radices(t.rad_th, d.col_group, &d.rad_th) ||
       !copy_radices(t.rad_filt, 1, &d.rad_filt)) {
     delete p;
@@ -325,6 +326,7 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
 
   TablePacker tp;
   const size_t o_tw_rho = tp.add(t.tw_rho), o_tw_r2c = tp.add(t.tw_r2c), o_tw_th = tp.add(t.tw_th);
+  const size_t o_tw_col = tp.add(t.tw_col);
   const size_t o_kf = tp.add(t.k_fwd), o_kb = tp.add(t.k_bp);
   const size_t o_frow = tp.add(t.fwd_row), o_fm = tp.add(t.fwd_m), o_fe = tp.add(t.fwd_e), o_fea = tp.add(t.fwd_eanc);
   const size_t o_fang = tp.add(t.fwd_ang), o_fanc = tp.add(t.fwd_anc);
@@ -343,6 +345,7 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.tw_rho = reinterpret_cast<const float2*>(tb + o_tw_rho);
   d.tw_r2c = reinterpret_cast<const float2*>(tb + o_tw_r2c);
   d.tw_th = reinterpret_cast<const float2*>(tb + o_tw_th);
+  d.tw_col = reinterpret_cast<const float2*>(tb + o_tw_col);
   d.k_fwd = reinterpret_cast<const float2*>(tb + o_kf);
   d.k_bp = reinterpret_cast<const float2*>(tb + o_kb);
   d.fwd_row = reinterpret_cast<const float4*>(tb + o_frow);
@@ -372,6 +375,12 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
     cudaGetLastError();
     radon_plan_destroy(p);
     return e == cudaErrorInvalidValue ? RADON_NOT_SUPPORTED : status_of(e);
+  }
+  if (d.col_fixed >= 0) {  // the specialised in-place column kernel is the default where it exists
+    radon::DevPlan f = d;
+    f.col_group = 0;
+    if (radon::configure_kernels(f) == cudaSuccess) d = f;
+    cudaGetLastError();
   }
   p->info.column_group = d.col_group;
   *out = p;
@@ -458,12 +467,15 @@ int radon_backproject_batch(radon_plan plan, const float* d_sinos, float* d_imag
 }
 
 int radon_plan_set_column_group(radon_plan plan, int group) {
-  if (!plan || (group != 1 && group != 2 && group != 4)) return RADON_INVALID_ARG;
+  if (!plan || (group != 0 && group != 1 && group != 2 && group != 4)) return RADON_INVALID_ARG;
   radon::DevPlan d = plan->dp;
   d.col_group = group;
-  radon::HostTables t;
-  radon::Radices rad;
-  if (!radon::factor_radices(d.n_theta, &rad) || !copy_radices(rad, group, &d.rad_th)) return RADON_NOT_SUPPORTED;
+  if (group == 0) {
+    if (d.col_fixed < 0) return RADON_NOT_SUPPORTED;
+  } else {
+    radon::Radices rad;
+    if (!radon::factor_radices(d.n_theta, &rad) || !copy_radices(rad, group, &d.rad_th)) return RADON_NOT_SUPPORTED;
+  }
   if (radon::configure_kernels(d) != cudaSuccess) return RADON_NOT_SUPPORTED;
   plan->dp = d;
   plan->info.column_group = group;

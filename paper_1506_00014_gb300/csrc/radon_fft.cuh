@@ -280,4 +280,183 @@ __device__ __forceinline__ void stage_table(float2* dst, const float2* __restric
   for (int i = tid; i < n; i += nth) dst[i] = __ldg(src + i);
 }
 
+
+// ------------------------------------------------------------------------------------------
+// In-place passes of compile-time shape.  Dft<R> runs one radix-R
+// butterfly in registers; idx(r) is the register that holds output r.
+
+template <int R, bool INV>
+struct Dft {
+  __host__ __device__ static constexpr int idx(int r) { return r; }
+  __device__ __forceinline__ static void run(float2 (&v)[R]) { dft<R, INV>(v); }
+};
+
+// Internal twiddles exp(-2 pi i q / R) of the composite radices below, as constants (q is known
+// at compile time once the butterfly is unrolled).
+template <int R>
+struct Wconst;
+template <>
+struct Wconst<16> {  // q = n2 k1 in {0, 1, 2, 3, 4, 6, 9}
+  __device__ __forceinline__ static float2 get(int q) {
+    constexpr float c1 = 0.923879532511286756f;  // cos(pi / 8)
+    constexpr float s1 = 0.382683432365089772f;  // sin(pi / 8)
+    constexpr float h = 0.707106781186547524f;   // cos(pi / 4)
+    switch (q) {
+      case 1: return make_float2(c1, -s1);
+      case 2: return make_float2(h, -h);
+      case 3: return make_float2(s1, -c1);
+      case 4: return make_float2(0.f, -1.f);
+      case 6: return make_float2(-h, -h);
+      case 9: return make_float2(-c1, s1);
+      default: return make_float2(1.f, 0.f);
+    }
+  }
+};
+template <>
+struct Wconst<14> {  // q = n2 k1 in {0, ..., 6}: cos(pi q / 7) - i sin(pi q / 7)
+  __device__ __forceinline__ static float2 get(int q) {
+    constexpr float c1 = 0.900968867902419126f, s1 = 0.433883739117558120f;
+    constexpr float c2 = 0.623489801858733531f, s2 = 0.781831482468029809f;
+    constexpr float c3 = 0.222520933956314404f, s3 = 0.974927912181823607f;
+    switch (q) {
+      case 1: return make_float2(c1, -s1);
+      case 2: return make_float2(c2, -s2);
+      case 3: return make_float2(c3, -s3);
+      case 4: return make_float2(-c3, -s3);
+      case 5: return make_float2(-c2, -s2);
+      case 6: return make_float2(-c1, -s1);
+      default: return make_float2(1.f, 0.f);
+    }
+  }
+};
+
+// R = R1 R2 Cooley-Tukey in registers: R1-point DFTs over n1 (input n = R2 n1 + n2), twiddles
+// W_R^(n2 k1), R2-point DFTs over n2; X[k1 + R1 k2] is left at v[R2 k1 + k2].
+template <int R1, int R2, bool INV>
+struct DftComposite {
+  static constexpr int R = R1 * R2;
+  __host__ __device__ static constexpr int idx(int r) { return R2 * (r % R1) + r / R1; }
+  __device__ __forceinline__ static void run(float2 (&v)[R]) {
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+      float2 c[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) c[n1] = v[R2 * n1 + n2];
+      dft<R1, INV>(c);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) {
+        float2 t = c[k1];
+        if (n2 * k1 != 0) {
+          const float2 w = Wconst<R>::get(n2 * k1);
+          t = INV ? cmulc(t, w) : cmul(t, w);
+        }
+        v[R2 * k1 + n2] = t;
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      float2 c[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) c[n2] = v[R2 * k1 + n2];
+      dft<R2, INV>(c);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) v[R2 * k1 + k2] = c[k2];
+    }
+  }
+};
+template <bool INV>
+struct Dft<16, INV> : DftComposite<4, 4, INV> {};
+template <bool INV>
+struct Dft<14, INV> : DftComposite<2, 7, INV> {};
+
+// Twiddle entries a pass of radix R after NS combined points reads: NS (R - 1), laid out
+// [k][r - 1] = exp(-2 pi i r k / (NS R)); none for the first pass (NS = 1).
+__host__ __device__ constexpr int pass_twiddles(int R, int NS) { return NS > 1 ? NS * (R - 1) : 0; }
+
+// One in-place Stockham pass over G interleaved transforms of length NN ([row][g] layout):
+// butterfly t = tid + i TH (t < G NN / R) handles transform g = t % G, index j = t / G.  Each thread holds BM
+// butterflies in registers from before the barrier (the whole array is read) until after it
+// (the whole array is written).  `in(row, g)` loads, `out(row, g, value)` stores; Out::kShared
+// says whether the stores go to shared memory and so need a barrier before the next pass.
+template <int NN, int G, int TH, int R, int NS, bool INV, class In, class Out>
+__device__ __forceinline__ void inplace_pass(const float2* __restrict__ tw, const In& in, const Out& out, int tid) {
+  constexpr int NBF = NN / R;
+  constexpr int NB = G * NBF;               // butterflies of the pass
+  constexpr int BM = (NB + TH - 1) / TH;    // per thread (the last round may be partial)
+  constexpr bool kExact = BM * TH == NB;
+  float2 v[BM][R];
+#pragma unroll
+  for (int i = 0; i < BM; ++i) {
+    const int t = tid + i * TH;
+    if (!kExact && t >= NB) break;
+    const int g = t % G, j = t / G;
+    const int k = j % NS;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[i][r] = in(j + r * NBF, g);
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tw[k * (R - 1) + r - 1];
+        v[i][r] = INV ? cmulc(v[i][r], w) : cmul(v[i][r], w);
+      }
+    }
+    Dft<R, INV>::run(v[i]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < BM; ++i) {
+    const int t = tid + i * TH;
+    if (!kExact && t >= NB) break;
+    const int g = t % G, j = t / G;
+    const int k = j % NS, q = j / NS;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out(q * NS * R + k + r * NS, g, v[i][Dft<R, INV>::idx(r)]);
+  }
+  if constexpr (Out::kShared) __syncthreads();
+}
+
+// Interleaved shared-memory views used between passes.
+template <int G>
+struct SmemIn {
+  const float2* d;
+  __device__ __forceinline__ float2 operator()(int row, int g) const { return d[row * G + g]; }
+};
+template <int G>
+struct SmemOut {
+  static constexpr bool kShared = true;
+  float2* d;
+  __device__ __forceinline__ void operator()(int row, int g, float2 v) const { d[row * G + g] = v; }
+};
+
+// A whole transform as a chain of in-place passes Rs... (first radix first); the first pass reads
+// through `in`, the last writes through `out`, the others use `data`.  TWO is the offset of the
+// current pass in the concatenated per-pass twiddle table.
+template <int NN, int G, int TH, bool INV, int NS, int TWO, int R, int... Rest>
+struct InplaceChain {
+  template <class In, class Out>
+  __device__ __forceinline__ static void run(const float2* __restrict__ tw, const In& in, float2* data,
+                                             const Out& out, int tid) {
+    if constexpr (sizeof...(Rest) == 0) {
+      inplace_pass<NN, G, TH, R, NS, INV>(tw + TWO, in, out, tid);
+    } else {
+      inplace_pass<NN, G, TH, R, NS, INV>(tw + TWO, in, SmemOut<G>{data}, tid);
+      InplaceChain<NN, G, TH, INV, NS * R, TWO + pass_twiddles(R, NS), Rest...>::run(tw, SmemIn<G>{data}, data, out,
+                                                                                      tid);
+    }
+  }
+};
+
+template <int... Rs>
+__host__ __device__ constexpr int chain_length() {
+  int n = 1;
+  ((n *= Rs), ...);
+  return n;
+}
+template <int... Rs>
+__host__ __device__ constexpr int chain_twiddles() {
+  int ns = 1, t = 0;
+  ((t += pass_twiddles(Rs, ns), ns *= Rs), ...);
+  return t;
+}
+
 }  // namespace radon

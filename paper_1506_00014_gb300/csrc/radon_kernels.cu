@@ -493,6 +493,122 @@ __global__ void __launch_bounds__(kThreads) k_columns(DevPlan p, const float2* _
   }
 }
 
+// Specialised column kernel for n_theta = product of Rs: one work item is G rho frequencies of
+// one partition, held interleaved ([row][g]) in shared
+// memory and transformed in place.  The first forward pass reads the spectrum rows straight from
+// global memory (rows outside the centre half are zero), the last forward pass multiplies by the
+// kernel, and the last inverse pass writes only the kept rows (centre half plus halo).  The grid
+// is persistent; the per-pass twiddles are staged once per CTA.
+template <int G>
+struct ColumnLoad {
+  const float2* x;  // spectrum rows of this partition, x_pitch apart
+  int x_pitch, nh, kr0, nc;
+  __device__ __forceinline__ float2 operator()(int row, int g) const {
+    const int jj = row - nh / 2;
+    const bool live = jj >= 0 && jj < nh && kr0 + g <= nc;
+    return live ? x[static_cast<size_t>(jj) * x_pitch + kr0 + g] : make_float2(0.f, 0.f);
+  }
+};
+template <int G, int NN>
+struct ColumnKernelStore {
+  static constexpr bool kShared = true;
+  float2* d;
+  const float2* kern;  // [k_rho][k_theta], k_theta in [0, NN / 2]
+  int kr0, nc;
+  __device__ __forceinline__ void operator()(int row, int g, float2 v) const {
+    const int kt = row <= NN - row ? row : NN - row;
+    const int kr = kr0 + g <= nc ? kr0 + g : nc;  // columns past nc are computed but never stored
+    d[row * G + g] = cmul(v, kern[static_cast<size_t>(kr) * (NN / 2 + 1) + kt]);
+  }
+};
+template <int G, int NN>
+struct ColumnStore {
+  static constexpr bool kShared = false;
+  float2* y;  // kept rows of this partition, x_pitch apart
+  int x_pitch, nh, kr0, nc;
+  __device__ __forceinline__ void operator()(int row, int g, float2 v) const {
+    const int jr = (row - nh / 2 + kHaloLo + NN) % NN;  // the convolution output is NN-periodic
+    if (jr < nh + kHaloLo + kHaloHi && kr0 + g <= nc) y[static_cast<size_t>(jr) * x_pitch + kr0 + g] = v;
+  }
+};
+
+template <int G, int TH, int MINB, int... Rs>
+__global__ void __launch_bounds__(TH, MINB) k_columns_fixed(DevPlan p, const float2* __restrict__ kern, int n_items) {
+  constexpr int NN = chain_length<Rs...>();
+  constexpr int NTW = chain_twiddles<Rs...>();
+  extern __shared__ __align__(16) float2 smem[];
+  float2* data = smem;
+  float2* tw = smem + NN * G;
+  stage_table(tw, p.tw_col, NTW, threadIdx.x, blockDim.x);
+  // (the first pass's barrier orders these stores before any twiddle read)
+  const int ngroups = (p.nc + G) / G;
+  const int nrow = p.nh + kHaloLo + kHaloHi;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int gi = w % ngroups, mb = w / ngroups;
+    const int m = mb % p.M, b = mb / p.M;
+    const int kr0 = gi * G;
+    const ColumnLoad<G> in{p.xspec + b * p.bs_x + static_cast<size_t>(m) * p.nh * p.x_pitch, p.x_pitch, p.nh, kr0,
+                           p.nc};
+    const ColumnKernelStore<G, NN> mul{data, kern, kr0, p.nc};
+    InplaceChain<NN, G, TH, false, 1, 0, Rs...>::run(tw, in, data, mul, threadIdx.x);
+    const ColumnStore<G, NN> out{p.yspec + b * p.bs_ys + static_cast<size_t>(m) * nrow * p.x_pitch, p.x_pitch, p.nh,
+                                 kr0, p.nc};
+    InplaceChain<NN, G, TH, true, 1, 0, Rs...>::run(tw, SmemIn<G>{data}, data, out, threadIdx.x);
+  }
+}
+
+template <int G, int TH, int MINB, int... Rs>
+constexpr bool column_radices_match(const ColumnRadices& c) {
+  int i = 0;
+  bool ok = c.G == G && c.TH == TH && c.MINB == MINB;
+  ((ok = ok && i < 4 && c.r[i] == Rs, ++i), ...);
+  return ok && (i == 4 || c.r[i] == 0) && c.n == chain_length<Rs...>();
+}
+
+// The instantiations, in kColumnRadices order.
+#define RADON_COLUMN_KERNELS(X)  \
+  X(0, 32, 256, 2, 16, 16)       \
+  X(1, 16, 256, 2, 8, 8, 8)      \
+  X(2, 8, 256, 2, 16, 8, 8)      \
+  X(3, 4, 256, 2, 16, 16, 8)     \
+  X(4, 2, 256, 2, 16, 16, 16)    \
+  X(5, 1, 256, 2, 16, 16, 16, 2) \
+  X(6, 4, 196, 2, 14, 14, 7)
+
+#define RADON_CHECK_COLUMN(i, ...) \
+  static_assert(column_radices_match<__VA_ARGS__>(kColumnRadices[i]), "column radix table");
+RADON_COLUMN_KERNELS(RADON_CHECK_COLUMN)
+#undef RADON_CHECK_COLUMN
+static_assert(kNumColumnRadices == 7, "every kColumnRadices entry has an instantiation");
+
+template <int G, int TH, int MINB, int... Rs>
+size_t columns_fixed_smem() {
+  constexpr int NN = chain_length<Rs...>();
+  return (static_cast<size_t>(NN) * G + chain_twiddles<Rs...>()) * sizeof(float2);
+}
+
+template <int G, int TH, int MINB, int... Rs>
+cudaError_t launch_columns_fixed(const DevPlan& p, const float2* kern, cudaStream_t st, int batch) {
+  const int n_items = (p.nc + G) / G * p.M * batch;
+  const int grid = n_items < p.col_blocks ? n_items : p.col_blocks;
+  k_columns_fixed<G, TH, MINB, Rs...><<<grid, TH, columns_fixed_smem<G, TH, MINB, Rs...>(), st>>>(p, kern, n_items);
+  return cudaSuccess;
+}
+
+// Raises the kernel's shared memory limit and sizes its persistent grid (resident CTAs).
+template <int G, int TH, int MINB, int... Rs>
+cudaError_t configure_columns_fixed(DevPlan& p, int optin, int n_sm) {
+  const size_t smem = columns_fixed_smem<G, TH, MINB, Rs...>();
+  if (smem > static_cast<size_t>(optin)) return cudaErrorInvalidValue;
+  auto* fn = k_columns_fixed<G, TH, MINB, Rs...>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TH, smem);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidValue;
+  p.col_blocks = per_sm * n_sm;
+  return e;
+}
+
 // Inverse real FFT along rho of one kept row; writes N_rho values plus kPad wrap columns per side.
 __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
   extern __shared__ __align__(16) float2 smem[];
@@ -701,8 +817,18 @@ size_t cols_smem(const DevPlan& p) { return (2 * static_cast<size_t>(p.col_group
 
 void launch_columns_and_inverse(const DevPlan& p, const float2* kern, cudaStream_t st, const StageHook& hook,
                                 int stage0, int batch) {
-  const int ngroups = (p.nc + 1 + p.col_group - 1) / p.col_group;
-  k_columns<<<dim3(ngroups, p.M, batch), kThreads, cols_smem(p), st>>>(p, kern);
+  if (p.col_group == 0) {
+#define RADON_LAUNCH_COLUMN(i, ...) \
+  case i: launch_columns_fixed<__VA_ARGS__>(p, kern, st, batch); break;
+    switch (p.col_fixed) {
+      RADON_COLUMN_KERNELS(RADON_LAUNCH_COLUMN)
+      default: break;
+    }
+#undef RADON_LAUNCH_COLUMN
+  } else {
+    const int ngroups = (p.nc + 1 + p.col_group - 1) / p.col_group;
+    k_columns<<<dim3(ngroups, p.M, batch), kThreads, cols_smem(p), st>>>(p, kern);
+  }
   hook(stage0, st);
   k_rows_inv<<<dim3(p.nh + kHaloLo + kHaloHi, p.M, batch), kThreads, rows_smem(p), st>>>(p);
   hook(stage0 + 1, st);
@@ -730,6 +856,19 @@ cudaError_t configure_kernels(DevPlan& p) {
   if ((e = cudaFuncSetAttribute(k_rows_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess) return e;
+  p.col_blocks = 0;
+  if (p.col_fixed >= 0) {
+    int n_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+#define RADON_CONFIGURE_COLUMN(i, ...) \
+  case i: e = configure_columns_fixed<__VA_ARGS__>(p, optin, n_sm); break;
+    switch (p.col_fixed) {
+      RADON_COLUMN_KERNELS(RADON_CONFIGURE_COLUMN)
+      default: e = cudaErrorInvalidValue;
+    }
+#undef RADON_CONFIGURE_COLUMN
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 

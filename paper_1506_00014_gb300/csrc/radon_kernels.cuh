@@ -18,7 +18,9 @@ struct DevPlan {
   int x_pitch;     // complex spectrum rows: >= N_rho/2 + 1
   int y_pitch;     // real log-polar rows with periodic wrap columns: >= N_rho + 2 kPad
   int n_eanc, n_ktiles, n_ptiles;
-  int col_group;   // rho frequencies per column CTA (4, 2 or 1: shared memory bound)
+  int col_group;   // generic column kernel: rho frequencies per CTA (4, 2 or 1); 0: specialised kernel
+  int col_fixed;   // kColumnRadices index of the specialised column kernel, -1 if none
+  int col_blocks;  // persistent grid of the specialised column kernel (resident CTAs on the device)
   int live_lo, live_hi;  // detector bins with |s| < 1 are exactly [live_lo, live_hi]
   float inv_drho, inv_dphi, inv_aR, d_s;
   RadixList rad_rho, rad_th;
@@ -26,6 +28,7 @@ struct DevPlan {
   const float2* tw_rho;
   const float2* tw_r2c;
   const float2* tw_th;
+  const float2* tw_col;  // per-pass twiddles of the specialised column transform
   const float2* k_fwd;
   const float2* k_bp;
   const float4* fwd_row;

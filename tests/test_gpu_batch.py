@@ -71,6 +71,33 @@ def test_column_group_does_not_change_results(rl):
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
 
 
+def test_specialised_column_kernel_matches_generic(rl):
+    """Group 0 (in-place power-of-two column FFT) equals the generic kernel up to FP32 rounding;
+    it is the default where n_theta allows it and refused elsewhere."""
+    N, na, nd = 128, 384, 192  # n_theta = 256
+    plan = rl.radon_plan_create(N, na, nd, 3, 3)
+    assert plan.info["n_theta"] == 256 and plan.info["column_group"] == 0
+    f = _t(ellipse_image(N, random_ellipses(10, 2)))
+    g = torch.randn((na, nd), device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    res = {}
+    for grp in (0, 1, 4):
+        rl.radon_plan_set_column_group(plan, grp)
+        s = torch.empty((na, nd), device="cuda")
+        b = torch.empty((N, N), device="cuda")
+        rl.radon_forward(plan, f, s)
+        rl.radon_backproject(plan, g, b)
+        res[grp] = (s, b)
+    for k in range(2):
+        a, ref = res[0][k], res[1][k]
+        assert float((a - ref).norm() / ref.norm()) < 2e-6
+        assert torch.equal(res[1][k], res[4][k])
+    other = rl.radon_plan_create(128, 128, 192, 3, 3)  # n_theta = 96: generic only
+    assert other.info["column_group"] in (1, 2, 4)
+    with pytest.raises(rl.RadonError) as err:
+        rl.radon_plan_set_column_group(other, 0)
+    assert err.value.status == 5  # RADON_NOT_SUPPORTED
+
+
 def test_uneven_batch_with_graph_matches_per_slice(rl):
     from paper_1506_00014_gb300.batch import UnevenBatch
 

@@ -63,6 +63,10 @@ CASES = [
     (64, 37, 90, 3, 5),      # M = 5, odd angle count
     (16, 12, 24, 3, 3),      # tiny
     (16, 5, 20, 1, 3),       # tiny, linear, n_theta_half = 2
+    (128, 384, 192, 3, 3),   # n_theta = 256: specialised in-place column kernel (16 x 16)
+    (160, 1024, 240, 1, 4),  # n_theta = 512 (8 x 8 x 8), M = 4, linear
+    (96, 1536, 150, 3, 3),   # n_theta = 1024 (16 x 8 x 8)
+    (64, 2048, 96, 3, 3),    # n_theta = 1372 (14 x 14 x 7, 196 threads)
 ]
 
 
