@@ -189,6 +189,7 @@ def run_ours(args):
 
     plan = rl.radon_plan_create(N, N_ANGLES, N_DET, INTERP, M)
     info = plan.info
+    launches_per_step = rl.radon_plan_kernel_launches(plan, "forward") + rl.radon_plan_kernel_launches(plan, "backproject")
     f = ellipse_image(N, random_ellipses(50, 2 + 1000 * rank)).astype(np.float32)
     g = random_sinogram(N_ANGLES, N_DET, 3 + 1000 * rank).astype(np.float32)
     f_d = torch.from_numpy(f).to(dev)
@@ -289,7 +290,7 @@ def run_ours(args):
         },
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "stage_ms_per_launch": stage_ms,
         "pixel_angle_updates_per_s": world * N * N * N_ANGLES * args.steps / (total_ms / 1e3),

@@ -149,6 +149,11 @@ int radon_kernel_quadrant(int N, int n_angles, int n_det, int n_partitions, int 
 int radon_profile_enable(radon_plan plan, int enable);
 int radon_profile_read(radon_plan plan, double* ms, int* launches);
 
+/* Number of kernels one call launches with the plan's current settings: op 0 radon_forward,
+ * 1 radon_backproject, 2 radon_fbp (a stage may launch more than one kernel).  Written to *out;
+ * RADON_INVALID_ARG for another op. */
+int radon_plan_kernel_launches(radon_plan plan, int op, int* out);
+
 /* Forward transform R without any allocation, for callers that must not allocate device memory
  * when they run a transform: code that runs under a framework owning every device allocation
  * (where a raw cudaMalloc is forbidden or would fragment its pool), or a real-time loop with a

@@ -26,6 +26,7 @@ from .binding import (  # noqa: F401
     radon_plan_get_info,
     radon_plan_reserve_batch,
     radon_plan_set_column_group,
+    radon_plan_kernel_launches,
     radon_profile_enable,
     radon_profile_read,
     radon_status_string,

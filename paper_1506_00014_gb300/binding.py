@@ -40,6 +40,7 @@ EXPORTED = (
     "radon_geometry", "radon_kernel_quadrant", "radon_status_string", "radon_profile_enable",
     "radon_profile_read", "radon_forward_static_scratch", "radon_plan_reserve_batch",
     "radon_forward_batch", "radon_backproject_batch", "radon_plan_set_column_group",
+    "radon_plan_kernel_launches",
 )
 
 RADON_NUM_STAGES = 11
@@ -83,6 +84,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.radon_kernel_quadrant.argtypes = [_c_int, _c_int, _c_int, _c_int, _c_int, P(ctypes.c_double)]
     lib.radon_plan_reserve_batch.argtypes = [_c_void_p, _c_int]
     lib.radon_plan_set_column_group.argtypes = [_c_void_p, _c_int]
+    lib.radon_plan_kernel_launches.argtypes = [_c_void_p, _c_int, P(_c_int)]
     for name in ("radon_forward_batch", "radon_backproject_batch"):
         getattr(lib, name).argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_void_p]
     lib.radon_profile_enable.argtypes = [_c_void_p, _c_int]
@@ -250,6 +252,14 @@ def radon_profile_read(plan: RadonPlan):
     n = (_c_int * RADON_NUM_STAGES)()
     _check(load().radon_profile_read(plan.handle, ms, n), "radon_profile_read")
     return {STAGE_NAMES[i]: (ms[i], n[i]) for i in range(RADON_NUM_STAGES)}
+
+
+def radon_plan_kernel_launches(plan: RadonPlan, op: str) -> int:
+    """Kernels one call of op ("forward", "backproject" or "fbp") launches."""
+    n = _c_int()
+    code = {"forward": 0, "backproject": 1, "fbp": 2}[op]
+    _check(load().radon_plan_kernel_launches(plan.handle, code, ctypes.byref(n)), "radon_plan_kernel_launches")
+    return n.value
 
 
 def radon_plan_reserve_batch(plan: RadonPlan, max_batch: int):

@@ -283,6 +283,62 @@ int build_tables(const radon_plan_info& g, HostTables* t) {
     hilo(u0, &t->fwd_m[4 * m], &t->fwd_m[4 * m + 1]);
     hilo(v0, &t->fwd_m[4 * m + 2], &t->fwd_m[4 * m + 3]);
   }
+  // Fine samples worth reading: the position (col, row) = (C0 + t Cv, R0 + t Rv), t = e^rho, is a
+  // line in t.  Keep t where the 4 x 4 tap block lies inside the padded array (col, row in
+  // [1, P - 2), shrunk by 1e-3 of a pixel for the FP32 positions) and where the block is within
+  // kDiscMargin (+ 1.5 for the integer block corner) pixels of the disc; map the t interval to
+  // rho indices i (rho_i = (i - N_rho + 1) d_rho).
+  t->fwd_rng.resize(2 * static_cast<size_t>(M) * nh * r);
+  {
+    const double P = N + 2.0 * kPad, lo_b = 1.0 + 1e-3, hi_b = P - 2.0 - 1e-3;
+    const double cz = kPad + N / 2.0, Rd = N / 2.0 + kDiscMargin + 1.5;
+    for (int m = 0; m < M; ++m) {
+      const double C0 = N / 2.0 - (1.0 - aR) * std::cos(m * beta) * S + kPad;
+      const double R0 = N / 2.0 - (1.0 - aR) * std::sin(m * beta) * S + kPad;
+      for (int jj = 0; jj < nh; ++jj)
+        for (int q = 0; q < r; ++q) {
+          const double phi = (jj + nh / 2 - nh) * g.d_phi + (q - 0.5 * (r - 1)) * g.d_phi / r;
+          const double Cv = std::cos(phi + m * beta) * S, Rv = std::sin(phi + m * beta) * S;
+          double tl = 0.0, th = 1e300;
+          auto clip_linear = [&](double x0, double v) {  // lo_b <= x0 + t v <= hi_b
+            if (v == 0.0) {
+              if (x0 < lo_b || x0 > hi_b) th = -1.0;
+              return;
+            }
+            const double a = (lo_b - x0) / v, b = (hi_b - x0) / v;
+            tl = std::max(tl, std::min(a, b));
+            th = std::min(th, std::max(a, b));
+          };
+          clip_linear(C0, Cv);
+          clip_linear(R0, Rv);
+          // |(C0 - cz, R0 - cz) + t (Cv, Rv)|^2 <= Rd^2
+          const double dx = C0 - cz, dy = R0 - cz;
+          const double A = Cv * Cv + Rv * Rv, B = 2.0 * (dx * Cv + dy * Rv), Cq = dx * dx + dy * dy - Rd * Rd;
+          const double disc = B * B - 4.0 * A * Cq;
+          if (disc < 0.0) {
+            th = -1.0;
+          } else {
+            const double sq = std::sqrt(disc);
+            tl = std::max(tl, (-B - sq) / (2.0 * A));
+            th = std::min(th, (-B + sq) / (2.0 * A));
+          }
+          int32_t ilo = 1, ihi = 0;
+          if (th > tl && th > 0.0) {
+            const double il = tl > 0.0 ? std::log(tl) / g.d_rho + nr - 1 : -1.0;
+            const double ih = std::log(th) / g.d_rho + nr - 1;
+            ilo = static_cast<int32_t>(std::max(0.0, std::ceil(il)));
+            ihi = static_cast<int32_t>(std::min(static_cast<double>(nr - 1), std::floor(ih)));
+            if (ilo > ihi) {
+              ilo = 1;
+              ihi = 0;
+            }
+          }
+          const size_t o = 2 * ((static_cast<size_t>(m) * nh + jj) * r + q);
+          t->fwd_rng[o] = ilo;
+          t->fwd_rng[o + 1] = ihi;
+        }
+    }
+  }
   const int n_eanc = (nr + kETile - 1) / kETile;
   t->fwd_e.resize(2 * static_cast<size_t>(nr));
   t->fwd_eanc.resize(2 * static_cast<size_t>(n_eanc));

@@ -21,6 +21,8 @@ constexpr int kHaloLo = 2;   // output rows kept below the centre half of the an
 constexpr int kHaloHi = 2;   // and above it (cubic taps of |phi| <= beta/2)
 constexpr int kPad = 3;      // zero border around the coefficient arrays (cubic taps never leave it)
 constexpr int kFirHalf = 14; // one-sided length of the truncated pre-filter (|z|^15 ~ 2.7e-9)
+constexpr int kDiscMargin = 16;  // forward sampling skips fine samples farther than this many
+                                 // pixels outside the disc (coefficients there are below 1e-9)
 
 // Column (theta) transform lengths with a specialised in-place kernel: G columns per work item,
 // TH threads per CTA, at least MINB resident CTAs per SM, and the radix sequence (0 ends it).
@@ -68,6 +70,8 @@ struct HostTables {
   std::vector<float> fwd_m;    // 4 per m: column / row offset (hi, lo)
   std::vector<float> fwd_e;    // 2 per i: e^rho_i / r, e^rho_i - e^rho_anchor(i)
   std::vector<float> fwd_eanc; // 2 per anchor: e^rho_anchor hi/lo
+  std::vector<int32_t> fwd_rng; // 2 per (m, jj, q): rho samples [lo, hi] whose taps lie in the
+                                // padded array and within the disc margin (lo > hi: none)
   // forward output (Algorithm 1: resample from S_m^{-1} Omega_p to Sigma)
   std::vector<int32_t> fwd_ang;  // 4 per angle: m, flip, first tap row (halo index), frac (float bits)
   std::vector<int32_t> fwd_anc;  // 4 per (angle, k tile): I, F (float bits), g (float bits), 0

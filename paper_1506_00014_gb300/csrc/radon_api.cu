@@ -329,6 +329,7 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   const size_t o_tw_col = tp.add(t.tw_col);
   const size_t o_kf = tp.add(t.k_fwd), o_kb = tp.add(t.k_bp);
   const size_t o_frow = tp.add(t.fwd_row), o_fm = tp.add(t.fwd_m), o_fe = tp.add(t.fwd_e), o_fea = tp.add(t.fwd_eanc);
+  const size_t o_frng = tp.add(t.fwd_rng);
   const size_t o_fang = tp.add(t.fwd_ang), o_fanc = tp.add(t.fwd_anc);
   const size_t o_bth = tp.add(t.bp_th), o_bc = tp.add(t.bp_c), o_be = tp.add(t.bp_e);
   const size_t o_banc = tp.add(t.bp_anc), o_bm = tp.add(t.bp_m), o_fir = tp.add(t.fir);
@@ -352,6 +353,7 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.fwd_m = reinterpret_cast<const float4*>(tb + o_fm);
   d.fwd_e = reinterpret_cast<const float2*>(tb + o_fe);
   d.fwd_eanc = reinterpret_cast<const float2*>(tb + o_fea);
+  d.fwd_rng = reinterpret_cast<const int2*>(tb + o_frng);
   d.fwd_ang = reinterpret_cast<const int4*>(tb + o_fang);
   d.fwd_anc = reinterpret_cast<const int4*>(tb + o_fanc);
   d.bp_th = reinterpret_cast<const int2*>(tb + o_bth);
@@ -479,6 +481,14 @@ int radon_plan_set_column_group(radon_plan plan, int group) {
   if (radon::configure_kernels(d) != cudaSuccess) return RADON_NOT_SUPPORTED;
   plan->dp = d;
   plan->info.column_group = group;
+  return RADON_OK;
+}
+
+int radon_plan_kernel_launches(radon_plan plan, int op, int* out) {
+  if (!plan || !out) return RADON_INVALID_ARG;
+  const int n = radon::kernel_launches(plan->dp, op);
+  if (n < 0) return RADON_INVALID_ARG;
+  *out = n;
   return RADON_OK;
 }
 

@@ -26,7 +26,6 @@ namespace radon {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kDiscMargin = 16;  // pixels beyond the unit disc still sampled by the forward rows
 
 __device__ __forceinline__ int odd_ext(int p, int n, float* sgn) {
   // extension of [0, n) that is odd about -1 and about n (period 2n + 2)
@@ -278,10 +277,6 @@ __device__ __forceinline__ float sample_image(const DevPlan& p, int b, int ic, f
 
 // Shared-memory layout of a forward row CTA (float2 units): bufA, bufB (nc each), the 16-byte
 // aligned anchor table (float4 per sub-angle and tile), the sub-angle directions, the twiddles.
-__host__ __device__ __forceinline__ int fwd_anchor_offset(const DevPlan& p) { return (2 * p.nc + 1) & ~1; }
-__host__ __device__ __forceinline__ int fwd_tw_offset(const DevPlan& p) {
-  return fwd_anchor_offset(p) + 2 * p.r * p.n_eanc + p.r + 1;
-}
 
 // Interpolant from the quad layout at padded index coordinates (ic + ac, ir + ar): one 16-byte
 // load per tap row.
@@ -312,47 +307,108 @@ __global__ void __launch_bounds__(kThreads) k_quad(DevPlan p) {
   }
 }
 
-__device__ void sample_row_forward(const DevPlan& p, int b, int m, int jj, float* __restrict__ h,
-                                   float4* __restrict__ anc, float2* __restrict__ dir) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Forward sampling (Algorithm 1: resample T_m f on Omega_lp, average the r sub-angles onto
+// Omega_p, multiply by e^rho).  One warp per tile of 32 rho samples of one angular row (m, jj);
+// a CTA holds the same tile of kSampleWarps adjacent rows, so its taps overlap in L1.  The real row h is written to the
+// spectrum scratch yspec (free until the theta convolution), 2 x_pitch floats per row.
+constexpr int kSampleWarps = 8;
+
+// Cubic B-spline weights times 6 (the 1/36 of a 2-D tap block is applied once per output).
+__device__ __forceinline__ void bspline_w6(float a, float (&w)[4]) {
+  const float om = 1.f - a;
+  const float a2 = a * a;
+  w[0] = om * om * om;
+  w[1] = fmaf(a2, fmaf(3.f, a, -6.f), 4.f);
+  w[2] = fmaf(a, fmaf(a, fmaf(-3.f, a, 3.f), 3.f), 1.f);
+  w[3] = a2 * a;
+}
+
+// Two rho samples per thread (i and i + 32, tiles 2 blockIdx.x and 2 blockIdx.x + 1) for each
+// sub-angle q; a sample is read only when i lies in the sub-angle's range fwd_rng (its taps are
+// then inside the padded array), so no per-sample bounds test is needed.
+template <bool QUAD>
+__global__ void __launch_bounds__(kSampleWarps * 32) k_sample_fwd(DevPlan p) {
+  extern __shared__ __align__(16) float4 sanc[];  // [warp][2][q] anchors, [warp][q] directions, [warp][q] ranges
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = p.r, ne = p.n_eanc;
-  const bool cubic = p.interp == 3;
+  const int tile0 = 2 * blockIdx.x, m = blockIdx.z % p.M, b = blockIdx.z / p.M;
+  const int jj = blockIdx.y * kSampleWarps + warp;
+  if (jj >= p.nh) return;  // whole warp; only warp-level synchronisation below
+  float4* anc = sanc + warp * 2 * r;
+  float2* dir = reinterpret_cast<float2*>(sanc + kSampleWarps * 2 * r) + warp * r;
+  int2* rng = reinterpret_cast<int2*>(reinterpret_cast<float2*>(sanc + kSampleWarps * 2 * r) + kSampleWarps * r) + warp * r;
   const float4 um = p.fwd_m[m];
-  const float4* rowc = p.fwd_row + (static_cast<size_t>(m) * p.nh + jj) * r;
-  for (int idx = threadIdx.x; idx < r * ne; idx += blockDim.x) {
-    const int q = idx / ne, tile = idx - q * ne;
+  const size_t row0 = (static_cast<size_t>(m) * p.nh + jj) * r;
+  const float4* rowc = p.fwd_row + row0;
+  const float2 ea0 = p.fwd_eanc[tile0];
+  const float2 ea1 = p.fwd_eanc[tile0 + 1 < ne ? tile0 + 1 : tile0];
+  for (int q = lane; q < r; q += 32) {
     const float4 cs = rowc[q];
-    const float2 ea = p.fwd_eanc[tile];
-    float ch, cl, rh, rl;
-    df_mul_add(ea.x, ea.y, cs.x, cs.y, um.x, um.y, &ch, &cl);
-    df_mul_add(ea.x, ea.y, cs.z, cs.w, um.z, um.w, &rh, &rl);
-    const float Ic = floorf(ch), Ir = floorf(rh);
-    anc[idx] = make_float4(Ic, (ch - Ic) + cl, Ir, (rh - Ir) + rl);
-    if (tile == 0) dir[q] = make_float2(cs.x, cs.z);
-  }
-  __syncthreads();
-  const int P = p.img_pitch, half = p.N / 2;
-  const unsigned reach2 = static_cast<unsigned>((half + kDiscMargin) * (half + kDiscMargin));
-  for (int tile = warp; tile < ne; tile += nw) {
-    const int i = tile * kETile + lane;
-    const bool valid = i < p.N_rho;
-    const float2 e = valid ? p.fwd_e[i] : make_float2(0.f, 0.f);
-    float acc = 0.f;
-    for (int q = 0; q < r; ++q) {
-      const float4 a = anc[q * ne + tile];
-      const float2 d = dir[q];
-      const float Fc = fmaf(e.y, d.x, a.y);
-      const float Fr = fmaf(e.y, d.y, a.w);
-      const float fc = floorf(Fc), fr = floorf(Fr);
-      const int ic = static_cast<int>(a.x + fc), ir = static_cast<int>(a.z + fr);  // padded indices
-      if (ic < 1 || ic > P - 3 || ir < 1 || ir > P - 3) continue;                 // every tap is zero
-      const int dx = ic - kPad - half, dy = ir - kPad - half;
-      if (static_cast<unsigned>(dx * dx) + static_cast<unsigned>(dy * dy) > reach2) continue;
-      acc += (p.img_quad && cubic) ? sample_image_quad(p, b, ic, Fc - fc, ir, Fr - fr)
-                                   : sample_image(p, b, ic, Fc - fc, ir, Fr - fr);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float2 ea = u ? ea1 : ea0;
+      float ch, cl, rh, rl;
+      df_mul_add(ea.x, ea.y, cs.x, cs.y, um.x, um.y, &ch, &cl);
+      df_mul_add(ea.x, ea.y, cs.z, cs.w, um.z, um.w, &rh, &rl);
+      const float Ic = floorf(ch), Ir = floorf(rh);
+      anc[u * r + q] = make_float4(Ic, (ch - Ic) + cl, Ir, (rh - Ir) + rl);
     }
-    if (valid) h[i] = acc * e.x;
+    dir[q] = make_float2(cs.x, cs.z);
+    rng[q] = p.fwd_rng[row0 + q];
   }
+  __syncwarp();
+  const int base = tile0 * kETile;
+  const int i0 = base + lane, i1 = i0 + kETile;
+  const float2 e0 = i0 < p.N_rho ? p.fwd_e[i0] : make_float2(0.f, 0.f);
+  const float2 e1 = i1 < p.N_rho ? p.fwd_e[i1] : make_float2(0.f, 0.f);
+  const int P = p.img_pitch;
+  float acc0 = 0.f, acc1 = 0.f;
+  for (int q = 0; q < r; ++q) {
+    const int2 rg = rng[q];
+    if (rg.y < base || rg.x > base + 2 * kETile - 1) continue;  // warp-uniform: no sample in range
+    const bool ok0 = i0 >= rg.x && i0 <= rg.y, ok1 = i1 >= rg.x && i1 <= rg.y;
+    const float2 d = dir[q];
+    const float4 a0 = anc[q], a1 = anc[r + q];
+    const float Fc0 = fmaf(e0.y, d.x, a0.y), Fr0 = fmaf(e0.y, d.y, a0.w);
+    const float Fc1 = fmaf(e1.y, d.x, a1.y), Fr1 = fmaf(e1.y, d.y, a1.w);
+    const float fc0 = floorf(Fc0), fr0 = floorf(Fr0), fc1 = floorf(Fc1), fr1 = floorf(Fr1);
+    // padded tap-block corners; samples out of range read element (1, 1) and are dropped
+    const int ic0 = ok0 ? static_cast<int>(a0.x + fc0) : 1, ir0 = ok0 ? static_cast<int>(a0.z + fr0) : 1;
+    const int ic1 = ok1 ? static_cast<int>(a1.x + fc1) : 1, ir1 = ok1 ? static_cast<int>(a1.z + fr1) : 1;
+    if constexpr (QUAD) {
+      const float4* __restrict__ img = p.coef_q4 + b * p.bs_img;
+      const float4* p0 = img + static_cast<size_t>(ir0 - 1) * P + (ic0 - 1);
+      const float4* p1 = img + static_cast<size_t>(ir1 - 1) * P + (ic1 - 1);
+      float4 v0[4], v1[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v0[k] = __ldg(p0 + k * P);
+        v1[k] = __ldg(p1 + k * P);
+      }
+      float wc[4], wr[4], s0 = 0.f, s1 = 0.f;
+      bspline_w6(Fc0 - fc0, wc);
+      bspline_w6(Fr0 - fr0, wr);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        s0 = fmaf(wr[k], fmaf(wc[0], v0[k].x, fmaf(wc[1], v0[k].y, fmaf(wc[2], v0[k].z, wc[3] * v0[k].w))), s0);
+      bspline_w6(Fc1 - fc1, wc);
+      bspline_w6(Fr1 - fr1, wr);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        s1 = fmaf(wr[k], fmaf(wc[0], v1[k].x, fmaf(wc[1], v1[k].y, fmaf(wc[2], v1[k].z, wc[3] * v1[k].w))), s1);
+      acc0 += ok0 ? s0 : 0.f;
+      acc1 += ok1 ? s1 : 0.f;
+    } else {
+      const float s0 = sample_image(p, b, ic0, Fc0 - fc0, ir0, Fr0 - fr0);
+      const float s1 = sample_image(p, b, ic1, Fc1 - fc1, ir1, Fr1 - fr1);
+      acc0 += ok0 ? s0 : 0.f;
+      acc1 += ok1 ? s1 : 0.f;
+    }
+  }
+  const float scale = QUAD ? 1.f / 36.f : 1.f;
+  float* h = reinterpret_cast<float*>(p.yspec + b * p.bs_ys + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch);
+  if (i0 < p.N_rho) h[i0] = acc0 * e0.x * scale;
+  if (i1 < p.N_rho) h[i1] = acc1 * e1.x * scale;
 }
 
 // Back-projection: G(phi_j, rho_i) = g~(phi_j + m beta, (e^rho_i - (1 - a_R) cos phi_j) / a_R).
@@ -431,12 +487,12 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
     if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
     tw = p.rows_tw_smem ? tws : p.tw_rho;
     sample_row_backproject(p, b, m, jj, reinterpret_cast<float*>(bufA));
-  } else {
-    float4* anc = reinterpret_cast<float4*>(smem + fwd_anchor_offset(p));
-    float2* tws = smem + fwd_tw_offset(p);
+  } else {  // the row sampled by k_sample_fwd, read as nc complex values
+    float2* tws = smem + 2 * nc;
     if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
     tw = p.rows_tw_smem ? tws : p.tw_rho;
-    sample_row_forward(p, b, m, jj, reinterpret_cast<float*>(bufA), anc, reinterpret_cast<float2*>(anc + p.r * p.n_eanc));
+    const float2* h = p.yspec + b * p.bs_ys + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) bufA[k] = h[k];
   }
   __syncthreads();
   const float2* Z = fft_block<false>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
@@ -810,8 +866,8 @@ size_t filt_smem(const DevPlan& p) {
 size_t rows_smem(const DevPlan& p) {
   return (2 + (p.rows_tw_smem ? 1 : 0)) * static_cast<size_t>(p.nc) * sizeof(float2);
 }
-size_t rows_fwd_smem(const DevPlan& p) {
-  return (static_cast<size_t>(fwd_tw_offset(p)) + (p.rows_tw_smem ? p.nc : 0)) * sizeof(float2);
+size_t sample_fwd_smem(const DevPlan& p) {
+  return static_cast<size_t>(kSampleWarps) * p.r * (2 * sizeof(float4) + sizeof(float2) + sizeof(int2));
 }
 size_t cols_smem(const DevPlan& p) { return (2 * static_cast<size_t>(p.col_group) + 1) * p.n_theta * sizeof(float2); }
 
@@ -844,15 +900,17 @@ cudaError_t configure_kernels(DevPlan& p) {
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
   p.rows_tw_smem = 1;  // stage the rho twiddles in shared memory when everything fits
-  if (rows_fwd_smem(p) > static_cast<size_t>(optin) || rows_smem(p) > static_cast<size_t>(optin)) p.rows_tw_smem = 0;
+  if (rows_smem(p) > static_cast<size_t>(optin)) p.rows_tw_smem = 0;
   p.filt_tw_smem = 1;
   if (filt_smem(p) > static_cast<size_t>(optin)) p.filt_tw_smem = 0;
-  if (rows_fwd_smem(p) > static_cast<size_t>(optin) || rows_smem(p) > static_cast<size_t>(optin) ||
+  if (sample_fwd_smem(p) > static_cast<size_t>(optin) || rows_smem(p) > static_cast<size_t>(optin) ||
       cols_smem(p) > static_cast<size_t>(optin) || filt_smem(p) > static_cast<size_t>(optin))
     return cudaErrorInvalidValue;
   if ((e = cudaFuncSetAttribute(k_sino_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess) return e;
   const int rs = optin, cs = optin;
   if ((e = cudaFuncSetAttribute(k_rows_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_sample_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_sample_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_rows_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess) return e;
@@ -882,7 +940,12 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
   if (p.img_quad && p.interp == 3)
     k_quad<<<dim3((p.img_pitch + kThreads - 1) / kThreads, p.img_pitch, batch), kThreads, 0, st>>>(p);
   hook(0, st);
-  k_rows_fwd<false><<<dim3(p.nh, p.M, batch), kThreads, rows_fwd_smem(p), st>>>(p);
+  const dim3 sgrid((p.n_eanc + 1) / 2, (p.nh + kSampleWarps - 1) / kSampleWarps, p.M * batch);
+  if (p.img_quad && p.interp == 3)
+    k_sample_fwd<true><<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
+  else
+    k_sample_fwd<false><<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
+  k_rows_fwd<false><<<dim3(p.nh, p.M, batch), kThreads, rows_smem(p), st>>>(p);
   hook(1, st);
   launch_columns_and_inverse(p, p.k_fwd, st, hook, 2, batch);
   k_gather_sino<<<dim3((p.n_det + 127) / 128, p.n_angles, batch), 128, 0, st>>>(p, sino);
@@ -905,6 +968,12 @@ cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image
   k_gather_image<<<dim3(p.n_ptiles, p.n_ptiles, batch), dim3(kPTile, kPTile), 0, st>>>(p, image);
   hook(9, st);
   return cudaGetLastError();
+}
+
+int kernel_launches(const DevPlan& p, int op) {
+  const int fwd = 6 + ((p.img_quad && p.interp == 3) ? 1 : 0);  // prefilter, [quad], sample, rows, columns, rows_inv, gather
+  const int bp = 5;                                              // prefilter, rows, columns, rows_inv, gather
+  return op == 0 ? fwd : op == 1 ? bp : op == 2 ? bp + 1 : -1;
 }
 
 cudaError_t launch_fbp(const DevPlan& p, const float* sino, float* image, int filter, cudaStream_t st, StageHook hook) {

@@ -35,6 +35,7 @@ struct DevPlan {
   const float4* fwd_m;
   const float2* fwd_e;
   const float2* fwd_eanc;
+  const int2* fwd_rng;
   const int4* fwd_ang;
   const int4* fwd_anc;
   const int2* bp_th;
@@ -84,6 +85,9 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
 cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook,
                                int batch = 1);
 cudaError_t launch_fbp(const DevPlan& p, const float* sino, float* image, int filter, cudaStream_t st, StageHook hook);
+
+// Kernels launched by launch_forward (op 0), launch_backproject (1) and launch_fbp (2).
+int kernel_launches(const DevPlan& p, int op);
 
 // Dynamic shared memory limits are raised once per device.
 cudaError_t configure_kernels(DevPlan& p);

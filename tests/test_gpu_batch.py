@@ -53,9 +53,8 @@ def test_batch_capacity_limits(rl):
     with pytest.raises(rl.RadonError) as err:  # 20 x 4099 texture rows exceed the surface height
         rl.radon_plan_reserve_batch(big, 20)
     assert err.value.status == 5  # RADON_NOT_SUPPORTED
-    with pytest.raises(rl.RadonError) as err:  # so few angles at this size need too many sub-angles
-        rl.radon_plan_create(4096, 64, 96, 3, 3)
-    assert err.value.status == 5
+    few = rl.radon_plan_create(4096, 64, 96, 3, 3)  # few angles: many sub-angles per coarse angle
+    assert few.info["r"] > 32  # more than one anchor per lane in the sampling warps
 
 
 def test_column_group_does_not_change_results(rl):
