@@ -124,9 +124,11 @@ def stage_bytes(info):
     img = 4 * n * n
     sino = 4 * na * nd
     disc = 4 * math.pi / 4 * n * n       # coefficient pixels inside the disc (read once per launch)
+    lp_rows = mm * nh * nr * 4           # sampled real log-polar rows
     return {
         "prefilter_image": 2 * img,
-        "rows_fwd": disc + spec_in,
+        "sample_fwd": disc + lp_rows,
+        "rows_fwd": lp_rows + spec_in,
         "columns_fwd": spec_in + kern + spec_out,
         "rows_inv_fwd": spec_out + ylp,
         "gather_sino": ylp + sino,
@@ -136,6 +138,21 @@ def stage_bytes(info):
         "rows_inv_bp": spec_out + ylp,
         "gather_image": ylp + img,
     }
+
+
+def _dram_traffic() -> dict:
+    """Per-launch DRAM bytes by stage from the committed ncu summary (empty if absent)."""
+    out = {}
+    path = os.path.join(ROOT, "profiles", "dram_traffic_radon_pair_N2048.txt")
+    try:
+        with open(path) as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) == 2 and not line.startswith("#"):
+                    out[parts[0]] = float(parts[1])
+    except OSError:
+        pass
+    return out
 
 
 def reduce_max(value: float, dist, device) -> float:
@@ -239,14 +256,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = nbytes[dom] / (dom_ms / 1e3) / 1e9
     stage_ms = {k: round(v[0] / max(1, v[1]), 4) for k, v in stage.items()}
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as fh:
-                traffic = json.load(fh).get(dom)
-        except (OSError, ValueError):
-            traffic = None
+    traffic = _dram_traffic().get(dom)
 
     # end to end through the host-buffer C ABI entry points (pinned host memory)
     h_f = torch.from_numpy(f).pin_memory()

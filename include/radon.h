@@ -141,11 +141,12 @@ int radon_kernel_quadrant(int N, int n_angles, int n_det, int n_partitions, int 
  * stream after each of its kernel launches.  radon_profile_read waits for the recorded events,
  * adds each stage's elapsed milliseconds to ms[stage] and its launch count to launches[stage]
  * (arrays of RADON_NUM_STAGES entries, not cleared by the call), then forgets the events.
- * Stages: 0 image pre-filter, 1 forward row sampling + rho FFT, 2 forward theta convolution,
- * 3 forward inverse rho FFT, 4 sinogram gather, 5 sinogram pre-filter, 6 back-projection row
- * sampling + rho FFT, 7 back-projection theta convolution, 8 back-projection inverse rho FFT,
- * 9 image gather, 10 FBP filter along s. */
-#define RADON_NUM_STAGES 11
+ * Stages: 0 image pre-filter, 1 forward rho FFT of the sampled rows, 2 forward theta
+ * convolution, 3 forward inverse rho FFT, 4 sinogram gather, 5 sinogram pre-filter,
+ * 6 back-projection row sampling + rho FFT, 7 back-projection theta convolution,
+ * 8 back-projection inverse rho FFT, 9 image gather, 10 FBP filter along s, 11 forward row
+ * sampling (log-polar resampling of the image). */
+#define RADON_NUM_STAGES 12
 int radon_profile_enable(radon_plan plan, int enable);
 int radon_profile_read(radon_plan plan, double* ms, int* launches);
 

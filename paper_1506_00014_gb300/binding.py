@@ -43,10 +43,11 @@ EXPORTED = (
     "radon_plan_kernel_launches",
 )
 
-RADON_NUM_STAGES = 11
+RADON_NUM_STAGES = 12
 STAGE_NAMES = (
     "prefilter_image", "rows_fwd", "columns_fwd", "rows_inv_fwd", "gather_sino",
     "prefilter_sino", "rows_bp", "columns_bp", "rows_inv_bp", "gather_image", "sino_filter",
+    "sample_fwd",
 )
 
 _lib = None

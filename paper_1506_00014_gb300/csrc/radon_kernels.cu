@@ -945,6 +945,7 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
     k_sample_fwd<true><<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
   else
     k_sample_fwd<false><<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
+  hook(11, st);
   k_rows_fwd<false><<<dim3(p.nh, p.M, batch), kThreads, rows_smem(p), st>>>(p);
   hook(1, st);
   launch_columns_and_inverse(p, p.k_fwd, st, hook, 2, batch);
