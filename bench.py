@@ -258,6 +258,27 @@ def run_ours(args):
     stage_ms = {k: round(v[0] / max(1, v[1]), 4) for k, v in stage.items()}
     traffic = _dram_traffic().get(dom)
 
+    # the linear-interpolation variant of the same workload (same timing rules, fewer steps)
+    plan_lin = rl.radon_plan_create(N, N_ANGLES, N_DET, 1, M)
+    for _ in range(3):
+        flush.zero_()
+        rl.radon_forward(plan_lin, f_d, sino_d, stream)
+        rl.radon_backproject(plan_lin, g_d, img_d, stream)
+    n_lin = max(1, min(args.steps, 50))
+    ev_lin = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_lin)]
+    torch.cuda.synchronize()
+    for k in range(n_lin):
+        flush.zero_()
+        ev_lin[k][0].record(stream)
+        rl.radon_forward(plan_lin, f_d, sino_d, stream)
+        rl.radon_backproject(plan_lin, g_d, img_d, stream)
+        ev_lin[k][1].record(stream)
+    torch.cuda.synchronize()
+    lin_ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev_lin), dist if world > 1 else None, dev) / n_lin
+    linear = {"interp_order": 1, "ms_per_step": lin_ms, "steps": n_lin,
+              "value": whole_job_rate(world, _samples_per_step(), 1, lin_ms / 1e3), "unit": UNIT}
+    del plan_lin
+
     # end to end through the host-buffer C ABI entry points (pinned host memory)
     h_f = torch.from_numpy(f).pin_memory()
     h_g = torch.from_numpy(g).pin_memory()
@@ -281,8 +302,11 @@ def run_ours(args):
     }
 
     cpu = None
+    err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(f, g)
+        cpu, (ref_s, ref_i) = cpu_baseline(f, g)
+        err = {"R": rel_l2(h_s.numpy(), ref_s), "R#": rel_l2(h_i.numpy(), ref_i), "tolerance": 1e-5,
+               "oracle": "FP64 log-polar oracle (Algorithms 1 and 2, dense DFTs), same inputs", "metric": "relative L2"}
 
     if world > 1:
         dist.barrier()
@@ -299,6 +323,8 @@ def run_ours(args):
             "algorithmic_bytes": nbytes[dom], "ms_per_launch": dom_ms,
         },
         "cpu_baseline": cpu,
+        "err_vs_oracle": err,
+        "linear_variant": linear,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
@@ -308,9 +334,10 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(f, g, partitions=(0,)):
-    """FP64 oracle on the host cores: R and R# of the same inputs restricted to partition 0 (of 3);
-    kernel tables and DFT matrices are set up outside the timed interval."""
+def cpu_baseline(f, g, partitions=None):
+    """FP64 log-polar oracle on the host cores: R f and R# g of the same inputs, all partitions
+    (partitions=None) or the listed ones; kernel tables and DFT matrices are set up outside the
+    timed interval.  Returns (the cpu_baseline object, (R f, R# g))."""
     import numpy as np
 
     from oracle import geometry, kernels, logpolar
@@ -320,18 +347,24 @@ def cpu_baseline(f, g, partitions=(0,)):
     KB = kernels.multiplier(geo, "B")
     dft = logpolar._Dft(geo)
     t0 = time.perf_counter()
-    logpolar.forward(f.astype(np.float64), geo, K=KR, dft=dft, partitions=partitions)
-    logpolar.backproject(g.astype(np.float64), geo, K=KB, dft=dft, partitions=partitions)
+    rf = logpolar.forward(f.astype(np.float64), geo, K=KR, dft=dft, partitions=partitions)
+    bg = logpolar.backproject(g.astype(np.float64), geo, K=KB, dft=dft, partitions=partitions)
     dt = time.perf_counter() - t0
-    frac = len(partitions) / M
-    return {
-        "value": frac * _samples_per_step() / dt,
-        "unit": UNIT,
-        "cores": os.cpu_count(),
-        "kind": "oracle",
-        "sample": f"R and R# of the N=2048 workload restricted to partition(s) {list(partitions)} of {M} "
-                  f"({dt:.1f} s); value scaled by that fraction",
-    }
+    parts = list(range(M)) if partitions is None else list(partitions)
+    frac = len(parts) / M
+    sample = (f"R and R# of the whole N=2048 workload ({dt:.1f} s)" if frac == 1.0 else
+              f"R and R# of the N=2048 workload restricted to partition(s) {parts} of {M} "
+              f"({dt:.1f} s); value scaled by that fraction")
+    info = {"value": frac * _samples_per_step() / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": sample}
+    return info, (rf, bg)
+
+
+def rel_l2(got, ref) -> float:
+    import numpy as np
+
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm(np.asarray(got, dtype=np.float64) - ref) / np.linalg.norm(ref))
 
 
 def run_reference(args):
@@ -349,7 +382,7 @@ def run_reference(args):
     last = None
     t_start = time.perf_counter()
     for _ in range(args.steps):  # bounded: stop after ~2 minutes of oracle time
-        last = cpu_baseline(f, g)
+        last, _ = cpu_baseline(f, g, partitions=(0,))
         vals.append(last["value"])
         if time.perf_counter() - t_start > 120.0:
             break
