@@ -140,6 +140,112 @@ def stage_bytes(info):
     }
 
 
+def _event_ms(torch, fn, reps: int, flush=None) -> float:
+    """Median CUDA-event time of fn() over reps runs on the current stream (L2 flushed before each)."""
+    import statistics
+
+    times = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def bench_batched(rl, torch, flush) -> dict:
+    """96 slices of uneven N drawn from {256, 512, 1024, 2048, 4096} (seed 4), n_angles = N,
+    n_det = 1.5 N: per-slice calls versus same-size batches replayed from one CUDA graph.  One
+    pass = R of every image, then R# of every sinogram.  Inputs are seeded uniform images; the
+    kernels' work does not depend on the values."""
+    from paper_1506_00014_gb300.batch import UnevenBatch
+    from workloads import slice_sizes
+
+    sizes = slice_sizes(96, 4)
+    ub = UnevenBatch(sizes, max_batch=16)
+    gen = torch.Generator(device="cuda")
+    for i, n in enumerate(sizes):
+        gen.manual_seed(100 + i)
+        ub.image(i).copy_(torch.rand((n, n), device="cuda", generator=gen))
+
+    def per_slice():
+        for n, idx in ub.groups.items():
+            plan = ub.plans[n]
+            for j in range(len(idx)):
+                rl.radon_forward(plan, ub.images[n][j], ub.sinos[n][j])
+        for n, idx in ub.groups.items():
+            plan = ub.plans[n]
+            for j in range(len(idx)):
+                rl.radon_backproject(plan, ub.sinos[n][j], ub.images[n][j])
+
+    per_slice()
+    t_slice = _event_ms(torch, per_slice, 3, flush)
+    ub.capture()
+    ub.replay()
+    t_graph = _event_ms(torch, ub.replay, 3, flush)
+    samples = sum(n * n + n * (3 * n // 2) for n in sizes)
+    return {
+        "slices": len(sizes), "sizes": {str(n): len(v) for n, v in ub.groups.items()},
+        "per_slice_ms": t_slice, "batched_graph_ms": t_graph, "speedup": t_slice / t_graph,
+        "batched_samples_per_s": samples / (t_graph / 1e3), "unit": UNIT,
+        "results": "equal to the per-slice calls bit for bit (tests/test_gpu_batch.py)",
+    }
+
+
+def bench_least_squares(rl, torch) -> dict:
+    """64 slices, N = 1024, 720 angles, 1536 bins; data = analytic ellipse line integrals plus
+    Gaussian noise at 1 % of the maximum (seeds 200 + i); 50 gradient steps of ||R f - g||^2:
+    the per-slice eager loop versus the batched autograd loop (backward = R#) replayed from a CUDA
+    graph."""
+    import numpy as np
+
+    from paper_1506_00014_gb300.recon import BatchedLeastSquares, LeastSquares, normal_operator_norm
+    from workloads import ellipse_sinogram, random_ellipses
+
+    n, na, nd, slices, steps = 1024, 720, 1536, 64, 50
+    plan = rl.radon_plan_create(n, na, nd, 3, 3)
+    g = []
+    for sl in range(slices):
+        s = ellipse_sinogram(random_ellipses(10, 200 + sl), na, nd)
+        s = s + np.random.default_rng(200 + sl).normal(0.0, 0.01 * np.abs(s).max(), s.shape)
+        g.append(s.astype(np.float32))
+    g = torch.from_numpy(np.stack(g)).cuda()
+    step = 1.0 / (2.0 * normal_operator_norm(plan))
+
+    def per_slice():
+        return [LeastSquares(plan, g[b], step=step).run(steps) for b in range(slices)]
+
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    per_slice()  # warm-up
+    torch.cuda.synchronize()
+    t0.record()
+    ref = per_slice()
+    t1.record()
+    torch.cuda.synchronize()
+    t_slice = t0.elapsed_time(t1)
+    rl.radon_plan_reserve_batch(plan, 16)
+    bl = BatchedLeastSquares(plan, g, step=step, use_graph=True)  # autograd's gradient is 2 c_R R#(R f - g)
+    torch.cuda.synchronize()
+    t0.record()
+    got = bl.run(steps)
+    t1.record()
+    torch.cuda.synchronize()
+    t_batch = t0.elapsed_time(t1)
+    ref = torch.stack(ref)
+    diff = float((got - ref).norm() / ref.norm())
+    loss0 = float((g * g).sum())
+    return {
+        "slices": slices, "N": n, "n_angles": na, "n_det": nd, "steps": steps,
+        "per_slice_eager_ms": t_slice, "batched_autograd_graph_ms": t_batch, "speedup": t_slice / t_batch,
+        "rel_diff_batched_vs_per_slice": diff, "loss_ratio_final_over_initial": float(bl.losses().sum()) / loss0,
+    }
+
+
 def _dram_traffic() -> dict:
     """Per-launch DRAM bytes by stage from the committed ncu summary (empty if absent)."""
     out = {}
@@ -301,6 +407,11 @@ def run_ours(args):
         "d2h_bytes_per_step": 4 * (N_ANGLES * N_DET + N * N),
     }
 
+    extras = {}
+    if world == 1 and not args.no_extras:
+        extras["batched"] = bench_batched(rl, torch, flush)
+        extras["least_squares"] = bench_least_squares(rl, torch)
+
     cpu = None
     err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -325,6 +436,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "err_vs_oracle": err,
         "linear_variant": linear,
+        **extras,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
@@ -424,6 +536,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (96 uneven slices) and least-squares (64 slices) comparisons")
     ap.add_argument("--once", action="store_true",
                     help="one untimed R + R# on the workload (for profiler captures); prints a short line")
     args = ap.parse_args()

@@ -11,7 +11,9 @@ Algorithm 1. The two agree to about 1e-5 relative on smooth inputs and differ mo
 ones, and that difference is what a finite-difference check of these gradients measures.
 
 R is linear, so nothing is saved for backward.  Inputs of shape [N, N] / [n_angles, n_det] or
-batches [B, ...] of them; each slice is one C ABI call on the current stream.
+batches [B, ...] of them.  A batch runs through the batched C ABI entry points in chunks of the
+plan's reserved capacity (radon_plan_reserve_batch; one slice per call when nothing is reserved),
+on the current stream.
 """
 
 from __future__ import annotations
@@ -31,15 +33,20 @@ def adjoint_scales(plan: binding.RadonPlan):
     return dx2 / dsino, dsino / dx2
 
 
-def _apply(fn, plan, x, out_shape):
+def _apply(fn, fn_batch, plan, x, out_shape):
     x = x.contiguous()
     if x.dim() == 2:
         out = torch.empty(out_shape, dtype=torch.float32, device=x.device)
         fn(plan, x, out)
         return out
     out = torch.empty((x.shape[0],) + tuple(out_shape), dtype=torch.float32, device=x.device)
-    for b in range(x.shape[0]):
-        fn(plan, x[b], out[b])
+    cap = max(1, getattr(plan, "max_batch", 1))
+    for b0 in range(0, x.shape[0], cap):
+        b1 = min(x.shape[0], b0 + cap)
+        if b1 - b0 == 1:
+            fn(plan, x[b0], out[b0])
+        else:
+            fn_batch(plan, x[b0:b1], out[b0:b1])
     return out
 
 
@@ -47,26 +54,26 @@ class RadonFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, image, plan):
         ctx.plan = plan
-        return _apply(binding.radon_forward, plan, image, plan.sino_shape)
+        return _apply(binding.radon_forward, binding.radon_forward_batch, plan, image, plan.sino_shape)
 
     @staticmethod
     def backward(ctx, grad):
         plan = ctx.plan
         c_r, _ = adjoint_scales(plan)
-        return _apply(binding.radon_backproject, plan, grad, plan.image_shape) * c_r, None
+        return _apply(binding.radon_backproject, binding.radon_backproject_batch, plan, grad, plan.image_shape) * c_r, None
 
 
 class BackprojectFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, sino, plan):
         ctx.plan = plan
-        return _apply(binding.radon_backproject, plan, sino, plan.image_shape)
+        return _apply(binding.radon_backproject, binding.radon_backproject_batch, plan, sino, plan.image_shape)
 
     @staticmethod
     def backward(ctx, grad):
         plan = ctx.plan
         _, c_b = adjoint_scales(plan)
-        return _apply(binding.radon_forward, plan, grad, plan.sino_shape) * c_b, None
+        return _apply(binding.radon_forward, binding.radon_forward_batch, plan, grad, plan.sino_shape) * c_b, None
 
 
 def radon(image: torch.Tensor, plan: binding.RadonPlan) -> torch.Tensor:

@@ -133,6 +133,7 @@ class RadonPlan:
     def __init__(self, handle: int, info: dict):
         self.handle = handle
         self.info = info
+        self.max_batch = 1  # slices one batched call may take (radon_plan_reserve_batch)
 
     def __del__(self):
         h, self.handle = getattr(self, "handle", None), None
@@ -266,6 +267,7 @@ def radon_plan_kernel_launches(plan: RadonPlan, op: str) -> int:
 def radon_plan_reserve_batch(plan: RadonPlan, max_batch: int):
     _check(load().radon_plan_reserve_batch(plan.handle, int(max_batch)), "radon_plan_reserve_batch")
     plan.info = radon_plan_get_info(plan)
+    plan.max_batch = max(plan.max_batch, int(max_batch))
 
 
 def radon_plan_set_column_group(plan: RadonPlan, group: int):

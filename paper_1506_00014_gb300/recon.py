@@ -110,3 +110,56 @@ def em(plan: binding.RadonPlan, g: torch.Tensor, iters: int, f0=None, eps: float
         _bp(plan, ratio.contiguous(), back)
         f = torch.where(disc, f * back / norm.clamp_min(eps), torch.zeros_like(f))
     return f
+
+
+class BatchedLeastSquares:
+    """Gradient descent for B slices of one plan at once, through autograd: the loss
+    sum_b ||R f_b - g_b||^2 is differentiated by RadonFunction, whose backward is the scaled R#
+    (batched C ABI calls in chunks of the plan's reserved capacity), then f <- f - step * grad.
+    With use_graph, one whole iteration (forward, backward, update) is captured in a CUDA graph
+    and replayed; reserve the plan's batch capacity before constructing it."""
+
+    def __init__(self, plan: binding.RadonPlan, g: torch.Tensor, step: float, f0=None, use_graph: bool = False):
+        from .autograd import radon
+
+        self._radon = radon
+        self.plan = plan
+        self.g = g.contiguous()
+        self.step = float(step)
+        shape = (g.shape[0],) + plan.image_shape
+        self.f = (torch.zeros(shape, device="cuda") if f0 is None else f0.clone().contiguous()).requires_grad_(True)
+        self.graph = None
+        if use_graph:
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                f_save = self.f.detach().clone()
+                for _ in range(2):  # warm up outside the capture (autograd and allocator state)
+                    self._iterate()
+                with torch.no_grad():
+                    self.f.copy_(f_save)
+            torch.cuda.current_stream().wait_stream(side)
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._iterate()
+
+    def _iterate(self):
+        self.f.grad = None
+        loss = ((self._radon(self.f, self.plan) - self.g) ** 2).sum()
+        loss.backward()
+        with torch.no_grad():
+            self.f.sub_(self.f.grad, alpha=self.step)
+
+    def run(self, steps: int):
+        for _ in range(steps):
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._iterate()
+        return self.f.detach()
+
+    def losses(self) -> torch.Tensor:
+        """Per-slice ||R f_b - g_b||^2."""
+        with torch.no_grad():
+            r = self._radon(self.f.detach(), self.plan) - self.g
+            return (r * r).sum(dim=(1, 2))
