@@ -197,6 +197,12 @@ int column_radices_index(int n_theta) {
   return -1;
 }
 
+int row_radices_index(int nc) {
+  for (int i = 0; i < kNumRowRadices; ++i)
+    if (kRowRadices[i].n == nc) return i;
+  return -1;
+}
+
 int build_tables(const radon_plan_info& g, HostTables* t) {
   const int N = g.N, na = g.n_angles, nd = g.n_det, M = g.n_partitions;
   const int nh = g.n_theta_half, nt = g.n_theta, nr = g.N_rho, nc = nr / 2, r = g.r;

@@ -40,6 +40,20 @@ constexpr int kNumColumnRadices = sizeof(kColumnRadices) / sizeof(kColumnRadices
 // Index into kColumnRadices, or -1 when n_theta has no specialised kernel.
 int column_radices_index(int n_theta);
 
+// Row (rho) complex transform lengths N_rho / 2 with a compile-time radix sequence (0 ends it).
+// The compiled transform uses the same twiddle table as the generic one, not the plan's radix list.
+struct RowRadices {
+  int n;
+  int r[5];
+};
+constexpr RowRadices kRowRadices[] = {
+    {2187, {9, 9, 9, 3, 0}},  // N = 2048, M = 3
+    {4374, {2, 9, 9, 9, 3}},  // N = 4096, M = 3
+    {1120, {8, 4, 5, 7, 0}},  // N = 1024, M = 3
+};
+constexpr int kNumRowRadices = sizeof(kRowRadices) / sizeof(kRowRadices[0]);
+int row_radices_index(int nc);  // index into kRowRadices, or -1
+
 struct Radices {
   int n = 0;
   int count = 0;

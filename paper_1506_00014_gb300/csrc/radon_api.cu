@@ -318,6 +318,7 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.d_s = static_cast<float>(g.d_s);
   d.n_filt = g.n_filter;
   d.col_fixed = t.col_fixed;
+  d.row_fixed = radon::row_radices_index(g.N_rho / 2);
   if (!copy_radices(t.rad_rho, 1, &d.rad_rho) || !copy_radices(t.rad_th, d.col_group, &d.rad_th) ||
       !copy_radices(t.rad_filt, 1, &d.rad_filt)) {
     delete p;

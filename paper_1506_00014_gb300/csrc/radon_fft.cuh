@@ -275,6 +275,48 @@ __device__ float2* fft_block(float2* a, float2* b, int nb, int fs, const RadixLi
   return a;
 }
 
+// The same Stockham transform with a compile-time radix sequence (one transform, TH threads):
+// index division by NS becomes a multiply-shift and the butterfly loop unrolls.  Same twiddle
+// table as fft_block: tw[p] = exp(-2 pi i p / NN).
+template <int NN, int R, int NS, bool INV, int TH>
+__device__ __forceinline__ void stockham_pass_fixed(const float2* __restrict__ src, float2* __restrict__ dst,
+                                                    const float2* __restrict__ tw, int tid) {
+  constexpr int NBF = NN / R, TSTEP = NN / (NS * R);
+#pragma unroll
+  for (int t0 = 0; t0 < NBF; t0 += TH) {
+    const int j = t0 + tid;
+    if (NBF % TH != 0 && j >= NBF) break;
+    const int q = j / NS, k = j - q * NS;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[j + r * NBF];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tw[r * k * TSTEP];
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      }
+    }
+    dft<R, INV>(v);
+    float2* d = dst + q * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[r * NS] = v[r];
+  }
+}
+
+template <int NN, bool INV, int TH, int NS, int R, int... Rest>
+struct FixedFft {
+  // Ping-pongs between a and b; returns the buffer holding the result.
+  __device__ __forceinline__ static float2* run(float2* a, float2* b, const float2* __restrict__ tw, int tid) {
+    stockham_pass_fixed<NN, R, NS, INV, TH>(a, b, tw, tid);
+    __syncthreads();
+    if constexpr (sizeof...(Rest) == 0)
+      return b;
+    else
+      return FixedFft<NN, INV, TH, NS * R, Rest...>::run(b, a, tw, tid);
+  }
+};
+
 // Copy an n-entry table into shared memory (all threads; caller synchronises).
 __device__ __forceinline__ void stage_table(float2* dst, const float2* __restrict__ src, int n, int tid, int nth) {
   for (int i = tid; i < n; i += nth) dst[i] = __ldg(src + i);

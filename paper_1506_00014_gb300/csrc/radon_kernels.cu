@@ -473,8 +473,45 @@ __device__ void sample_row_backproject(const DevPlan& p, int b, int m, int jj, f
   }
 }
 
+// Row transforms with a compile-time radix sequence, in kRowRadices order.
+#define RADON_ROW_SEQUENCES(X) \
+  X(0, 9, 9, 9, 3)             \
+  X(1, 2, 9, 9, 9, 3)          \
+  X(2, 8, 4, 5, 7)
+
+template <int... Rs>
+constexpr bool row_radices_match(const RowRadices& c) {
+  int i = 0;
+  bool ok = true;
+  ((ok = ok && i < 5 && c.r[i] == Rs, ++i), ...);
+  return ok && (i == 5 || c.r[i] == 0) && c.n == chain_length<Rs...>();
+}
+
+template <int SEQ, bool INV>
+struct RowFft;
+#define RADON_ROW_FFT(i, ...)                                                                              \
+  template <bool INV>                                                                                      \
+  struct RowFft<i, INV> {                                                                                  \
+    __device__ __forceinline__ static float2* run(float2* a, float2* b, const float2* __restrict__ tw) {    \
+      return FixedFft<chain_length<__VA_ARGS__>(), INV, kThreads, 1, __VA_ARGS__>::run(a, b, tw, threadIdx.x); \
+    }                                                                                                      \
+  };                                                                                                       \
+  static_assert(row_radices_match<__VA_ARGS__>(kRowRadices[i]), "row radix table");
+RADON_ROW_SEQUENCES(RADON_ROW_FFT)
+#undef RADON_ROW_FFT
+static_assert(kNumRowRadices == 3, "every kRowRadices entry has a compiled transform");
+
+// Complex transform of length nc along a row (all threads of the CTA); SEQ < 0: generic.
+template <bool INV, int SEQ>
+__device__ __forceinline__ const float2* row_fft(float2* a, float2* b, const DevPlan& p, const float2* tw) {
+  if constexpr (SEQ < 0)
+    return fft_block<INV>(a, b, 1, p.nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
+  else
+    return RowFft<SEQ, INV>::run(a, b, tw);
+}
+
 // Sample one angular row, real FFT along rho, write the half spectrum (N_rho/2 + 1 bins).
-template <bool BACK>
+template <bool BACK, int SEQ>
 __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
   extern __shared__ __align__(16) float2 smem[];
   const int nc = p.nc;
@@ -495,7 +532,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
     for (int k = threadIdx.x; k < nc; k += blockDim.x) bufA[k] = h[k];
   }
   __syncthreads();
-  const float2* Z = fft_block<false>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
+  const float2* Z = row_fft<false, SEQ>(bufA, bufB, p, tw);
   float2* out = p.xspec + b * p.bs_x + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch;
   for (int k = threadIdx.x; k <= nc; k += blockDim.x) {
     const float2 zk = Z[k == nc ? 0 : k];
@@ -666,6 +703,7 @@ cudaError_t configure_columns_fixed(DevPlan& p, int optin, int n_sm) {
 }
 
 // Inverse real FFT along rho of one kept row; writes N_rho values plus kPad wrap columns per side.
+template <int SEQ>
 __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
   extern __shared__ __align__(16) float2 smem[];
   const int nc = p.nc, nr = p.N_rho;
@@ -685,7 +723,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
     bufA[k] = make_float2(sm.x - df.y, sm.y + df.x);      // + i * df
   }
   __syncthreads();
-  const float2* Z = fft_block<true>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
+  const float2* Z = row_fft<true, SEQ>(bufA, bufB, p, tw);
   const float* h = reinterpret_cast<const float*>(Z);
   float* y = p.ylp + b * p.bs_y + (static_cast<size_t>(m) * nrow + row) * p.y_pitch;
   const int yrow = (b * p.M + m) * nrow + row;
@@ -871,6 +909,20 @@ size_t sample_fwd_smem(const DevPlan& p) {
 }
 size_t cols_smem(const DevPlan& p) { return (2 * static_cast<size_t>(p.col_group) + 1) * p.n_theta * sizeof(float2); }
 
+template <bool BACK>
+void launch_rows_forward(const DevPlan& p, cudaStream_t st, int batch) {
+  const dim3 grid(p.nh, p.M, batch);
+  // the back-projection rows keep the generic transform: with the compiled one its sampling
+  // part ran slower (measured 78 -> 92 us at N = 2048)
+  switch (BACK ? -1 : p.row_fixed) {
+#define RADON_LAUNCH_ROWS_FWD(i, ...) \
+  case i: k_rows_fwd<BACK, i><<<grid, kThreads, rows_smem(p), st>>>(p); break;
+    RADON_ROW_SEQUENCES(RADON_LAUNCH_ROWS_FWD)
+#undef RADON_LAUNCH_ROWS_FWD
+    default: k_rows_fwd<BACK, -1><<<grid, kThreads, rows_smem(p), st>>>(p); break;
+  }
+}
+
 void launch_columns_and_inverse(const DevPlan& p, const float2* kern, cudaStream_t st, const StageHook& hook,
                                 int stage0, int batch) {
   if (p.col_group == 0) {
@@ -886,7 +938,14 @@ void launch_columns_and_inverse(const DevPlan& p, const float2* kern, cudaStream
     k_columns<<<dim3(ngroups, p.M, batch), kThreads, cols_smem(p), st>>>(p, kern);
   }
   hook(stage0, st);
-  k_rows_inv<<<dim3(p.nh + kHaloLo + kHaloHi, p.M, batch), kThreads, rows_smem(p), st>>>(p);
+  const dim3 grid(p.nh + kHaloLo + kHaloHi, p.M, batch);
+  switch (p.row_fixed) {
+#define RADON_LAUNCH_ROWS_INV(i, ...) \
+  case i: k_rows_inv<i><<<grid, kThreads, rows_smem(p), st>>>(p); break;
+    RADON_ROW_SEQUENCES(RADON_LAUNCH_ROWS_INV)
+#undef RADON_LAUNCH_ROWS_INV
+    default: k_rows_inv<-1><<<grid, kThreads, rows_smem(p), st>>>(p); break;
+  }
   hook(stage0 + 1, st);
 }
 
@@ -908,11 +967,19 @@ cudaError_t configure_kernels(DevPlan& p) {
     return cudaErrorInvalidValue;
   if ((e = cudaFuncSetAttribute(k_sino_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess) return e;
   const int rs = optin, cs = optin;
-  if ((e = cudaFuncSetAttribute(k_rows_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_rows_fwd<false, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_sample_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_sample_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_rows_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_rows_fwd<true, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_rows_inv<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+#define RADON_CONFIGURE_ROWS(i, ...)                                                                                   \
+  if ((e = cudaFuncSetAttribute(k_rows_fwd<false, i>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) \
+    return e;                                                                                                          \
+  if ((e = cudaFuncSetAttribute(k_rows_fwd<true, i>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess)  \
+    return e;                                                                                                          \
+  if ((e = cudaFuncSetAttribute(k_rows_inv<i>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+  RADON_ROW_SEQUENCES(RADON_CONFIGURE_ROWS)
+#undef RADON_CONFIGURE_ROWS
   if ((e = cudaFuncSetAttribute(k_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess) return e;
   p.col_blocks = 0;
   if (p.col_fixed >= 0) {
@@ -946,7 +1013,7 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
   else
     k_sample_fwd<false><<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
   hook(11, st);
-  k_rows_fwd<false><<<dim3(p.nh, p.M, batch), kThreads, rows_smem(p), st>>>(p);
+  launch_rows_forward<false>(p, st, batch);
   hook(1, st);
   launch_columns_and_inverse(p, p.k_fwd, st, hook, 2, batch);
   k_gather_sino<<<dim3((p.n_det + 127) / 128, p.n_angles, batch), 128, 0, st>>>(p, sino);
@@ -963,7 +1030,7 @@ cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image
                             kThreads, 0, st>>>(p, ssrc, p.n_angles, p.n_det + 1, p.coef_sino, p.sino_pitch, 0, p.bs_sino, 0,
                                                0);
   hook(5, st);
-  k_rows_fwd<true><<<dim3(p.nh, p.M, batch), kThreads, rows_smem(p), st>>>(p);
+  launch_rows_forward<true>(p, st, batch);
   hook(6, st);
   launch_columns_and_inverse(p, p.k_bp, st, hook, 7, batch);
   k_gather_image<<<dim3(p.n_ptiles, p.n_ptiles, batch), dim3(kPTile, kPTile), 0, st>>>(p, image);
