@@ -666,7 +666,7 @@ constexpr bool column_radices_match(const ColumnRadices& c) {
   X(3, 4, 256, 2, 16, 16, 8)     \
   X(4, 2, 256, 2, 16, 16, 16)    \
   X(5, 1, 256, 2, 16, 16, 16, 2) \
-  X(6, 4, 196, 2, 14, 14, 7)
+  X(6, 4, 392, 2, 14, 14, 7)
 
 #define RADON_CHECK_COLUMN(i, ...) \
   static_assert(column_radices_match<__VA_ARGS__>(kColumnRadices[i]), "column radix table");
