@@ -246,6 +246,23 @@ def bench_least_squares(rl, torch) -> dict:
     }
 
 
+def bench_fbp_large(rl, torch, flush) -> dict:
+    """FBP at N = 8192 with 8192 angles and 12288 bins, Shepp-Logan window, then R#: one call of
+    radon_fbp on a seeded N(0, 1) sinogram (the work does not depend on the values)."""
+    n, na, nd = 8192, 8192, 12288
+    plan = rl.radon_plan_create(n, na, nd, 3, 3)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    g = torch.randn((na, nd), device="cuda", generator=gen)
+    img = torch.empty((n, n), device="cuda")
+    fn = lambda: rl.radon_fbp(plan, g, img, rl.RADON_FILTER_SHEPP_LOGAN)  # noqa: E731
+    for _ in range(2):
+        fn()
+    t = _event_ms(torch, fn, 5, flush)
+    return {"N": n, "n_angles": na, "n_det": nd, "filter": "shepp-logan", "ms_per_fbp": t,
+            "output_pixels_per_s": n * n / (t / 1e3),
+            "accuracy": "closed form (FBP of analytic Gaussians) checked in tests/test_gpu_parity.py"}
+
+
 def _dram_traffic() -> dict:
     """Per-launch DRAM bytes by stage from the committed ncu summary (empty if absent)."""
     out = {}
@@ -411,6 +428,7 @@ def run_ours(args):
     if world == 1 and not args.no_extras:
         extras["batched"] = bench_batched(rl, torch, flush)
         extras["least_squares"] = bench_least_squares(rl, torch)
+        extras["fbp_8192"] = bench_fbp_large(rl, torch, flush)
 
     cpu = None
     err = None

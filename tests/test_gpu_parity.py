@@ -253,3 +253,8 @@ def test_large_sizes_against_closed_forms(rl, N):
         bp += w * math.sqrt(2 * math.pi) * sg * direct.gaussian_bp(np.hypot(x[None, :] - cx, x[:, None] - cy), sg)
     bp[~geometry.disc_mask(N)] = 0.0
     assert _rel(_gpu_back(rl, plan, sino), bp) < 2e-5
+    # FBP with the Shepp-Logan window (Eq. FBP, Eq. SLfilt) of the analytic sinogram returns the
+    # Gaussians themselves on the disc (at N = 8192 this is the 8192 x 12288 FBP workload)
+    ref = np.where(geometry.disc_mask(N), gaussian_image(N, blobs), 0.0)
+    err = _rel(_gpu_fbp(rl, plan, sino, 1), ref)
+    assert err < 1e-3, err
