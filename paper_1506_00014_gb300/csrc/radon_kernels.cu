@@ -148,7 +148,13 @@ struct SinoSource {
   }
 };
 
-template <class Src>
+// QUAD: the tile's output is the quad-row layout coef_q4 (element (r, c) = padded coefficients
+// (r, c .. c+3), zero outside the image): kPfQuads quad origins per tile need the 64 coefficient
+// columns starting 3 to their left, which the tile computes as usual and then regroups in shared
+// memory.  Rows outside the image stay zero from allocation.
+constexpr int kPfQuads = kPfCols - 3;
+
+template <class Src, bool QUAD>
 __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int n_rows, int n_cols,
                                                         float* __restrict__ out, int out_pitch, int out_r0,
                                                         size_t out_bstride, cudaSurfaceObject_t surf, int surf_rows) {
@@ -158,7 +164,9 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
   src.slice(b);
   if (out) out += b * out_bstride;
   const int srow = b * surf_rows;
-  const int r0 = blockIdx.y * kPfRows - kFirHalf, c0 = blockIdx.x * kPfCols - kFirHalf;
+  const int qcol = blockIdx.x * kPfQuads;                       // first quad origin (QUAD)
+  const int ccol = QUAD ? qcol - 3 : blockIdx.x * kPfCols;      // first coefficient column computed
+  const int r0 = blockIdx.y * kPfRows - kFirHalf, c0 = ccol - kFirHalf;
   const int tid = threadIdx.x;
   if (src.interior(r0, r0 + kPfInR, c0, c0 + kPfInC)) {
     // all loads of this thread are issued before the first shared-memory store
@@ -183,8 +191,8 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
     }
   }
   __syncthreads();
-  const int orow = blockIdx.y * kPfRows, ocol = blockIdx.x * kPfCols;
-  if (p.interp == 1) {  // linear interpolation uses the masked samples themselves
+  const int orow = blockIdx.y * kPfRows, ocol = ccol;
+  if (!QUAD && p.interp == 1) {  // linear interpolation uses the masked samples themselves
     for (int idx = tid; idx < kPfRows * kPfCols; idx += kThreads) {
       const int ly = idx / kPfCols, lx = idx - ly * kPfCols;
       if (orow + ly < n_rows && ocol + lx < n_cols) {
@@ -226,10 +234,23 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
 #pragma unroll
       for (int n = 1; n <= kFirHalf; ++n) acc = fmaf(q[n], w[t + kFirHalf - n] + w[t + kFirHalf + n], acc);
       const int gr = orow + sy + t;
-      if (gr < n_rows && gc < n_cols) {
+      if constexpr (QUAD) {
+        s_in[sy + t][lx] = (gc >= 0 && gc < n_cols) ? acc : 0.f;  // s_in is free after the row pass
+      } else if (gr < n_rows && gc < n_cols) {
         if (out) out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = acc;
         if (surf) surf2Dwrite(acc, surf, gc * static_cast<int>(sizeof(float)), srow + gr);
       }
+    }
+  }
+  if constexpr (QUAD) {
+    __syncthreads();
+    const int P = p.img_pitch;
+    float4* q4 = p.coef_q4 + b * p.bs_img;
+    for (int idx = tid; idx < kPfRows * kPfQuads; idx += kThreads) {
+      const int y = idx / kPfQuads, lx = idx - y * kPfQuads;
+      const int gr = orow + y, c = qcol + lx;
+      if (gr < n_rows && c < P)
+        q4[static_cast<size_t>(gr + kPad) * P + c] = make_float4(s_in[y][lx], s_in[y][lx + 1], s_in[y][lx + 2], s_in[y][lx + 3]);
     }
   }
 }
@@ -294,18 +315,6 @@ __device__ __forceinline__ float sample_image_quad(const DevPlan& p, int b, int 
   return acc;
 }
 
-// Expands the padded coefficient image into the quad layout (one slice per blockIdx.z).
-__global__ void __launch_bounds__(kThreads) k_quad(DevPlan p) {
-  const int P = p.img_pitch, b = blockIdx.z;
-  const float* __restrict__ src = p.coef_img + b * p.bs_img;
-  float4* __restrict__ dst = p.coef_q4 + b * p.bs_img;
-  const int r = blockIdx.y;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P; c += gridDim.x * blockDim.x) {
-    const float* q = src + static_cast<size_t>(r) * P + c;
-    dst[static_cast<size_t>(r) * P + c] =
-        make_float4(q[0], c + 1 < P ? q[1] : 0.f, c + 2 < P ? q[2] : 0.f, c + 3 < P ? q[3] : 0.f);
-  }
-}
 
 // Forward sampling (Algorithm 1: resample T_m f on Omega_lp, average the r sub-angles onto
 // Omega_p, multiply by e^rho).  One warp per tile of 32 rho samples of one angular row (m, jj);
@@ -1002,10 +1011,12 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
   if (batch < 1 || batch > p.batch_cap) return cudaErrorInvalidValue;
   hook(-1, st);
   ImageSource isrc{image, p.N};
-  k_prefilter<ImageSource><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows, batch), kThreads, 0, st>>>(
-      p, isrc, p.N, p.N, p.coef_img, p.img_pitch, kPad, p.bs_img, 0, 0);
   if (p.img_quad && p.interp == 3)
-    k_quad<<<dim3((p.img_pitch + kThreads - 1) / kThreads, p.img_pitch, batch), kThreads, 0, st>>>(p);
+    k_prefilter<ImageSource, true><<<dim3((p.img_pitch + kPfQuads - 1) / kPfQuads, (p.N + kPfRows - 1) / kPfRows, batch),
+                                     kThreads, 0, st>>>(p, isrc, p.N, p.N, nullptr, 0, 0, 0, 0, 0);
+  else
+    k_prefilter<ImageSource, false><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows, batch),
+                                      kThreads, 0, st>>>(p, isrc, p.N, p.N, p.coef_img, p.img_pitch, kPad, p.bs_img, 0, 0);
   hook(0, st);
   const dim3 sgrid((p.n_eanc + 1) / 2, (p.nh + kSampleWarps - 1) / kSampleWarps, p.M * batch);
   if (p.img_quad && p.interp == 3)
@@ -1026,7 +1037,7 @@ cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image
   if (batch < 1 || batch > p.batch_cap) return cudaErrorInvalidValue;
   hook(-1, st);
   SinoSource ssrc{sino, p.n_angles, p.n_det, p.live_lo, p.live_hi};
-  k_prefilter<SinoSource><<<dim3((p.n_det + 1 + kPfCols - 1) / kPfCols, (p.n_angles + kPfRows - 1) / kPfRows, batch),
+  k_prefilter<SinoSource, false><<<dim3((p.n_det + 1 + kPfCols - 1) / kPfCols, (p.n_angles + kPfRows - 1) / kPfRows, batch),
                             kThreads, 0, st>>>(p, ssrc, p.n_angles, p.n_det + 1, p.coef_sino, p.sino_pitch, 0, p.bs_sino, 0,
                                                0);
   hook(5, st);
@@ -1039,8 +1050,8 @@ cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image
 }
 
 int kernel_launches(const DevPlan& p, int op) {
-  const int fwd = 6 + ((p.img_quad && p.interp == 3) ? 1 : 0);  // prefilter, [quad], sample, rows, columns, rows_inv, gather
-  const int bp = 5;                                              // prefilter, rows, columns, rows_inv, gather
+  const int fwd = 6;  // prefilter, sample, rows, columns, rows_inv, gather
+  const int bp = 5;   // prefilter, rows, columns, rows_inv, gather
   return op == 0 ? fwd : op == 1 ? bp : op == 2 ? bp + 1 : -1;
 }
 
