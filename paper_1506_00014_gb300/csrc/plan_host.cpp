@@ -459,7 +459,7 @@ int build_tables(const radon_plan_info& g, HostTables* t) {
         o[3] = fbits(Fr);
         o[4] = fbits(static_cast<float>(y1));
         o[5] = fbits(static_cast<float>(y2));
-        o[6] = 0;
+        o[6] = fbits(static_cast<float>(1.0 / (y1 * y1 + y2 * y2)));
         o[7] = 0;
       }
   }

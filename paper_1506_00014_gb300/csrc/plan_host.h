@@ -94,7 +94,7 @@ struct HostTables {
   std::vector<int32_t> bp_c;     // 2 per jj: -(1-a_R) cos(phi_j) / (a_R ds) + n_det/2 as (int, frac bits)
   std::vector<int32_t> bp_e;     // 2 per i: e^rho_i / (a_R ds) as (int, frac bits)
   // back-projection output (Algorithm 2: resample to X and sum the partitions)
-  std::vector<int32_t> bp_anc;   // 8 per (m, tile): I_theta, F_theta, I_rho, F_rho, y0x, y0y, 0, 0
+  std::vector<int32_t> bp_anc;   // 8 per (m, tile): I_theta, F_theta, I_rho, F_rho, y0x, y0y, 1/|y0|^2, 0
   std::vector<float> bp_m;       // 2 per m: a_R cos(m beta), a_R sin(m beta)
   std::vector<float> fir;        // kFirHalf + 1 pre-filter taps sqrt(3) z^n
   // FBP filter along s: real FFT of length n_filter (complex length n_filter / 2)

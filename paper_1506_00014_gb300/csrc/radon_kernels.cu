@@ -79,7 +79,7 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // atan(y/x) for x > 0 and |y/x| < 0.1 by its Maclaurin series x - x^3/3 + x^5/5 (remainder
 // below |y/x|^7 / 7 < 1.5e-8); other arguments use atan2f.
 __device__ __forceinline__ float small_atan2(float y, float x) {
-  const float t = y / x;
+  const float t = __fdividef(y, x);  // |t| < 0.1 on the fast path: a few ulp of a small angle
   if (!(x > 0.f) || fabsf(t) >= 0.1f) return atan2f(y, x);
   const float t2 = t * t;
   return t * fmaf(t2, fmaf(t2, 0.2f, -1.f / 3.f), 1.f);
@@ -749,8 +749,11 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
 // Output gathers.
 
 // Interpolant of partition m's log-polar coefficients at (halo row It + at, padded column
-// Ir + ar); taps are clamped into the array.  With use_tex the coefficients are read with
+// Ir + ar), times lp_gain(p) (36 for cubic: the weights are taken times 6 per axis and the caller
+// applies 1 / lp_gain once); taps are clamped into the array.  With use_tex the coefficients are read with
 // tex2Dgather from the CUDA array (partition m occupies rows [m nrow, (m+1) nrow)).
+__device__ __forceinline__ float lp_gain_inv(const DevPlan& p) { return p.interp == 3 ? 1.f / 36.f : 1.f; }
+
 __device__ __forceinline__ float sample_lp(const DevPlan& p, int b, int m, int It, float at, int Ir, float ar) {
   const int nrow = p.nh + kHaloLo + kHaloHi;
   const int pm = b * p.M + m;  // partition block in the (slice, partition)-stacked texture
@@ -758,8 +761,8 @@ __device__ __forceinline__ float sample_lp(const DevPlan& p, int b, int m, int I
     const cudaTextureObject_t t = p.tex_lp;
     if (p.interp == 3) {
       float wt[4], wr[4];
-      bspline_w(at, wt);
-      bspline_w(ar, wr);
+      bspline_w6(at, wt);
+      bspline_w6(ar, wr);
       const float y0 = static_cast<float>(pm * nrow + clampi(It - 1, 0, nrow - 4)) + 1.f, y1 = y0 + 2.f;
       const float x0 = static_cast<float>(clampi(Ir - 1, 0, p.y_pitch - 4)) + 1.f, x1 = x0 + 2.f;
       const float4 g00 = tex2Dgather<float4>(t, x0, y0, 0);
@@ -781,8 +784,8 @@ __device__ __forceinline__ float sample_lp(const DevPlan& p, int b, int m, int I
   const float* __restrict__ y = p.ylp + b * p.bs_y + static_cast<size_t>(m) * nrow * p.y_pitch;
   if (p.interp == 3) {
     float wt[4], wr[4];
-    bspline_w(at, wt);
-    bspline_w(ar, wr);
+    bspline_w6(at, wt);
+    bspline_w6(ar, wr);
     const int r0 = clampi(It - 1, 0, nrow - 4);
     const int c0 = clampi(Ir - 1, 0, p.y_pitch - 4);
     const float* base = y + static_cast<size_t>(r0) * p.y_pitch + c0;
@@ -817,7 +820,8 @@ __global__ void __launch_bounds__(128) k_gather_sino(DevPlan p, float* __restric
     const int n = k - (k / kKTile) * kKTile;
     const float cr = fmaf(log1pf(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
     const float fr = floorf(cr);
-    out = sample_lp(p, b, ang.x, ang.z, __int_as_float(ang.w), anc.x + static_cast<int>(fr), cr - fr) * p.inv_aR;
+    out = sample_lp(p, b, ang.x, ang.z, __int_as_float(ang.w), anc.x + static_cast<int>(fr), cr - fr) *
+          (p.inv_aR * lp_gain_inv(p));
   }
   sino[static_cast<size_t>(a) * nd + k] = out;
 }
@@ -845,14 +849,14 @@ __global__ void __launch_bounds__(kPTile * kPTile) k_gather_image(DevPlan p, flo
       const float r2 = fmaf(y0x, y0x, y0y * y0y);
       const float ydot = fmaf(y0x, dy1, y0y * dy2);
       const float dth = small_atan2(cross, r2 + ydot);
-      const float drho = 0.5f * small_log1p(fmaf(2.f, ydot, fmaf(dy1, dy1, dy2 * dy2)) / r2);
+      const float drho = 0.5f * small_log1p(fmaf(2.f, ydot, fmaf(dy1, dy1, dy2 * dy2)) * __int_as_float(a1.z));
       const float ct = fmaf(dth, p.inv_dphi, __int_as_float(a0.y));
       const float cr = fmaf(drho, p.inv_drho, __int_as_float(a0.w));
       const float ft = floorf(ct), fr = floorf(cr);
       acc += sample_lp(p, b, m, a0.x + static_cast<int>(ft), ct - ft, a0.z + static_cast<int>(fr), cr - fr);
     }
   }
-  img[static_cast<size_t>(i) * N + j] = acc;
+  img[static_cast<size_t>(i) * N + j] = acc * lp_gain_inv(p);
 }
 
 // FBP: filter one sinogram row along s (Eq. FBP, Eq. ramp / SLfilt / cosfilt).  The row (bins
