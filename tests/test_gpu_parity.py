@@ -184,6 +184,27 @@ def test_host_buffer_entry_points_match_device_ones(rl):
     assert np.array_equal(hi.astype(np.float64), _gpu_back(rl, plan, g))
 
 
+def test_kernel_launch_counts(rl):
+    plan = rl.radon_plan_create(64, 64, 96, 3, 3)
+    assert rl.radon_plan_kernel_launches(plan, "forward") == 6
+    assert rl.radon_plan_kernel_launches(plan, "backproject") == 5
+    assert rl.radon_plan_kernel_launches(plan, "fbp") == 6
+    assert rl.load().radon_plan_kernel_launches(plan.handle, 7, None) == 1  # RADON_INVALID_ARG
+    # the per-stage profile sees one launch per stage and call
+    rl.radon_profile_enable(plan, True)
+    rl.radon_profile_read(plan)
+    f = torch.zeros((64, 64), device="cuda")
+    s = torch.empty((64, 96), device="cuda")
+    rl.radon_forward(plan, f, s)
+    rl.radon_backproject(plan, s, f)
+    stages = rl.radon_profile_read(plan)
+    rl.radon_profile_enable(plan, False)
+    ran = {k for k, (ms, n) in stages.items() if n}
+    assert ran == {"prefilter_image", "sample_fwd", "rows_fwd", "columns_fwd", "rows_inv_fwd", "gather_sino",
+                   "prefilter_sino", "rows_bp", "columns_bp", "rows_inv_bp", "gather_image"}
+    assert all(n == 1 for k, (ms, n) in stages.items() if k in ran)
+
+
 def test_invalid_arguments_raise(rl):
     plan = rl.radon_plan_create(32, 32, 48, 3, 3)
     with pytest.raises(TypeError):

@@ -36,6 +36,13 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(declared) == set(lib.EXPORTED)
 
 
+def test_profiling_stage_table_matches_header(lib):
+    src = open(os.path.join(ROOT, "include", "radon.h")).read()
+    n = int(re.search(r"#define\s+RADON_NUM_STAGES\s+(\d+)", src).group(1))
+    assert lib.RADON_NUM_STAGES == n == len(lib.STAGE_NAMES)
+    assert len(set(lib.STAGE_NAMES)) == n
+
+
 @pytest.mark.parametrize("args", [(128, 128, 192, 3, 3), (2048, 2048, 3072, 3, 3), (1024, 720, 1536, 3, 3),
                                   (96, 100, 150, 1, 4), (8192, 8192, 12288, 3, 3), (64, 37, 90, 3, 5)])
 def test_geometry_matches_oracle_rules(lib, args):
