@@ -88,30 +88,49 @@ class UnevenBatch:
         self.graph.replay()
 
     # ---------------------------------------------------------------- autotuning
-    def tune(self, groups=(0, 1, 2, 4), repeats: int = 3):
-        """Choose each plan's column group by timing one batched R + R# (numerics unchanged).
-        Uses (and overwrites) the group buffers: set the inputs afterwards."""
+    def _time_group(self, n, repeats):
+        """Milliseconds of `repeats` passes of R then R# over group n with its current chunk."""
+        self._run_group(n)
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record()
+        for _ in range(repeats):
+            self._run_group(n)
+        stop.record()
+        torch.cuda.synchronize()
+        return start.elapsed_time(stop)
+
+    def _run_group(self, n):
+        plan, c = self.plans[n], self.chunk[n]
+        for s in range(0, len(self.groups[n]), c):
+            binding.radon_forward_batch(plan, self.images[n][s:s + c], self.sinos[n][s:s + c])
+        for s in range(0, len(self.groups[n]), c):
+            binding.radon_backproject_batch(plan, self.sinos[n][s:s + c], self.images[n][s:s + c])
+
+    def tune(self, groups=(0, 1, 2, 4), chunks=(1, 2, 4, 8, 16), repeats: int = 2):
+        """Per size group, choose the slices per batched call (up to the reserved capacity), then
+        the theta-convolution kernel, by timing R then R# over the whole group.  Neither choice
+        changes results beyond FP32 rounding of the theta kernel (chunking changes nothing).
+        Uses (and overwrites) the group buffers: set the inputs afterwards.  Returns
+        {N: (chunk, column group)}."""
         choice = {}
         for n, plan in self.plans.items():
-            c = self.chunk[n]
+            cap = self.chunk[n]
+            best = None
+            for c in sorted({min(c, cap) for c in chunks}):
+                self.chunk[n] = c
+                t = self._time_group(n, repeats)
+                if best is None or t < best[0]:
+                    best = (t, c)
+            self.chunk[n] = best[1]
             best = None
             for g in groups:
                 try:
                     binding.radon_plan_set_column_group(plan, g)
                 except binding.RadonError:
                     continue
-                img, sin = self.images[n][:c], self.sinos[n][:c]
-                binding.radon_forward_batch(plan, img, sin)
-                start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                start.record()
-                for _ in range(repeats):
-                    binding.radon_forward_batch(plan, img, sin)
-                    binding.radon_backproject_batch(plan, sin, img)
-                stop.record()
-                torch.cuda.synchronize()
-                t = start.elapsed_time(stop)
+                t = self._time_group(n, repeats)
                 if best is None or t < best[0]:
                     best = (t, g)
             binding.radon_plan_set_column_group(plan, best[1])
-            choice[n] = best[1]
+            choice[n] = (self.chunk[n], best[1])
         return choice

@@ -33,7 +33,7 @@ struct ColumnRadices {
 constexpr ColumnRadices kColumnRadices[] = {
     {256, 32, 256, 2, {16, 16, 0, 0}},  {512, 16, 256, 2, {8, 8, 8, 0}},     {1024, 8, 256, 2, {16, 8, 8, 0}},
     {2048, 4, 256, 2, {16, 16, 8, 0}},  {4096, 2, 256, 2, {16, 16, 16, 0}}, {8192, 1, 256, 2, {16, 16, 16, 2}},
-    {1372, 4, 392, 2, {14, 14, 7, 0}},
+    {1372, 4, 392, 2, {14, 14, 7, 0}},  {2744, 2, 392, 2, {14, 14, 14, 0}},
 };
 constexpr int kNumColumnRadices = sizeof(kColumnRadices) / sizeof(kColumnRadices[0]);
 

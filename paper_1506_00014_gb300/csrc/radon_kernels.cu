@@ -675,13 +675,14 @@ constexpr bool column_radices_match(const ColumnRadices& c) {
   X(3, 4, 256, 2, 16, 16, 8)     \
   X(4, 2, 256, 2, 16, 16, 16)    \
   X(5, 1, 256, 2, 16, 16, 16, 2) \
-  X(6, 4, 392, 2, 14, 14, 7)
+  X(6, 4, 392, 2, 14, 14, 7)    \
+  X(7, 2, 392, 2, 14, 14, 14)
 
 #define RADON_CHECK_COLUMN(i, ...) \
   static_assert(column_radices_match<__VA_ARGS__>(kColumnRadices[i]), "column radix table");
 RADON_COLUMN_KERNELS(RADON_CHECK_COLUMN)
 #undef RADON_CHECK_COLUMN
-static_assert(kNumColumnRadices == 7, "every kColumnRadices entry has an instantiation");
+static_assert(kNumColumnRadices == 8, "every kColumnRadices entry has an instantiation");
 
 template <int G, int TH, int MINB, int... Rs>
 size_t columns_fixed_smem() {

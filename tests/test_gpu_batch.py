@@ -104,6 +104,7 @@ def test_uneven_batch_with_graph_matches_per_slice(rl):
     ub = UnevenBatch(sizes, max_batch=2)
     choice = ub.tune()
     assert set(choice) == {64, 96, 128}
+    assert all(1 <= c <= 2 and g in (0, 1, 2, 4) for c, g in choice.values())
     imgs = [_t(ellipse_image(n, random_ellipses(6, 40 + i))) for i, n in enumerate(sizes)]
     ub.set_images(imgs)
     ub.forward()

@@ -66,7 +66,8 @@ CASES = [
     (128, 384, 192, 3, 3),   # n_theta = 256: specialised in-place column kernel (16 x 16)
     (160, 1024, 240, 1, 4),  # n_theta = 512 (8 x 8 x 8), M = 4, linear
     (96, 1536, 150, 3, 3),   # n_theta = 1024 (16 x 8 x 8)
-    (64, 2048, 96, 3, 3),    # n_theta = 1372 (14 x 14 x 7, 196 threads)
+    (64, 2048, 96, 3, 3),    # n_theta = 1372 (14 x 14 x 7, 392 threads)
+    (64, 4096, 96, 3, 3),    # n_theta = 2744 (14 x 14 x 14, 2 columns per work item)
 ]
 
 
