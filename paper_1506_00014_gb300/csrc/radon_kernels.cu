@@ -332,6 +332,18 @@ __device__ __forceinline__ void bspline_w6(float a, float (&w)[4]) {
   w[3] = a2 * a;
 }
 
+// bspline_w6 for two fractions at once (.x and .y), with paired FP32 arithmetic.
+__device__ __forceinline__ void bspline_w6_pair(float2 a, float2 (&w)[4]) {
+  const float2 one = make_float2(1.f, 1.f);
+  const float2 om = __ffma2_rn(a, make_float2(-1.f, -1.f), one);
+  const float2 a2 = __fmul2_rn(a, a);
+  w[0] = __fmul2_rn(__fmul2_rn(om, om), om);
+  w[1] = __ffma2_rn(a2, __ffma2_rn(make_float2(3.f, 3.f), a, make_float2(-6.f, -6.f)), make_float2(4.f, 4.f));
+  w[2] = __ffma2_rn(a, __ffma2_rn(a, __ffma2_rn(make_float2(-3.f, -3.f), a, make_float2(3.f, 3.f)), make_float2(3.f, 3.f)),
+                    one);
+  w[3] = __fmul2_rn(a2, a);
+}
+
 // Two rho samples per thread (i and i + 32, tiles 2 blockIdx.x and 2 blockIdx.x + 1) for each
 // sub-angle q; a sample is read only when i lies in the sub-angle's range fwd_rng (its taps are
 // then inside the padded array), so no per-sample bounds test is needed.
@@ -394,17 +406,15 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_sample_fwd(DevPlan p) {
         v0[k] = __ldg(p0 + k * P);
         v1[k] = __ldg(p1 + k * P);
       }
-      float wc[4], wr[4], s0 = 0.f, s1 = 0.f;
-      bspline_w6(Fc0 - fc0, wc);
-      bspline_w6(Fr0 - fr0, wr);
+      float2 wc[4], wr[4];  // .x: sample i0, .y: sample i1
+      bspline_w6_pair(make_float2(Fc0 - fc0, Fc1 - fc1), wc);
+      bspline_w6_pair(make_float2(Fr0 - fr0, Fr1 - fr1), wr);
+      float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        s0 = fmaf(wr[k], fmaf(wc[0], v0[k].x, fmaf(wc[1], v0[k].y, fmaf(wc[2], v0[k].z, wc[3] * v0[k].w))), s0);
-      bspline_w6(Fc1 - fc1, wc);
-      bspline_w6(Fr1 - fr1, wr);
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        s1 = fmaf(wr[k], fmaf(wc[0], v1[k].x, fmaf(wc[1], v1[k].y, fmaf(wc[2], v1[k].z, wc[3] * v1[k].w))), s1);
+      for (int k = 0; k < 4; ++k) {
+        s0 = fmaf(wr[k].x, fmaf(wc[0].x, v0[k].x, fmaf(wc[1].x, v0[k].y, fmaf(wc[2].x, v0[k].z, wc[3].x * v0[k].w))), s0);
+        s1 = fmaf(wr[k].y, fmaf(wc[0].y, v1[k].x, fmaf(wc[1].y, v1[k].y, fmaf(wc[2].y, v1[k].z, wc[3].y * v1[k].w))), s1);
+      }
       acc0 += ok0 ? s0 : 0.f;
       acc1 += ok1 ? s1 : 0.f;
     } else {
@@ -761,9 +771,9 @@ __device__ __forceinline__ float sample_lp(const DevPlan& p, int b, int m, int I
   if (p.use_tex) {
     const cudaTextureObject_t t = p.tex_lp;
     if (p.interp == 3) {
-      float wt[4], wr[4];
-      bspline_w6(at, wt);
-      bspline_w6(ar, wr);
+      float2 w[4];  // .x: theta weights, .y: rho weights
+      bspline_w6_pair(make_float2(at, ar), w);
+      const float wt[4] = {w[0].x, w[1].x, w[2].x, w[3].x}, wr[4] = {w[0].y, w[1].y, w[2].y, w[3].y};
       const float y0 = static_cast<float>(pm * nrow + clampi(It - 1, 0, nrow - 4)) + 1.f, y1 = y0 + 2.f;
       const float x0 = static_cast<float>(clampi(Ir - 1, 0, p.y_pitch - 4)) + 1.f, x1 = x0 + 2.f;
       const float4 g00 = tex2Dgather<float4>(t, x0, y0, 0);
@@ -784,9 +794,9 @@ __device__ __forceinline__ float sample_lp(const DevPlan& p, int b, int m, int I
   }
   const float* __restrict__ y = p.ylp + b * p.bs_y + static_cast<size_t>(m) * nrow * p.y_pitch;
   if (p.interp == 3) {
-    float wt[4], wr[4];
-    bspline_w6(at, wt);
-    bspline_w6(ar, wr);
+    float2 w[4];  // .x: theta weights, .y: rho weights
+    bspline_w6_pair(make_float2(at, ar), w);
+    const float wt[4] = {w[0].x, w[1].x, w[2].x, w[3].x}, wr[4] = {w[0].y, w[1].y, w[2].y, w[3].y};
     const int r0 = clampi(It - 1, 0, nrow - 4);
     const int c0 = clampi(Ir - 1, 0, p.y_pitch - 4);
     const float* base = y + static_cast<size_t>(r0) * p.y_pitch + c0;
