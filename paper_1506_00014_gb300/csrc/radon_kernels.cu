@@ -157,13 +157,12 @@ constexpr int kPfQuads = kPfCols - 3;
 template <class Src, bool QUAD>
 __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int n_rows, int n_cols,
                                                         float* __restrict__ out, int out_pitch, int out_r0,
-                                                        size_t out_bstride, cudaSurfaceObject_t surf, int surf_rows) {
+                                                        size_t out_bstride) {
   __shared__ float s_in[kPfInR][kPfInC + 1];
   __shared__ float s_mid[kPfInR][kPfCols + 1];
   const int b = blockIdx.z;  // slice of a batch
   src.slice(b);
   if (out) out += b * out_bstride;
-  const int srow = b * surf_rows;
   const int qcol = blockIdx.x * kPfQuads;                       // first quad origin (QUAD)
   const int ccol = QUAD ? qcol - 3 : blockIdx.x * kPfCols;      // first coefficient column computed
   const int r0 = blockIdx.y * kPfRows - kFirHalf, c0 = ccol - kFirHalf;
@@ -197,8 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
       const int ly = idx / kPfCols, lx = idx - ly * kPfCols;
       if (orow + ly < n_rows && ocol + lx < n_cols) {
         const float v = s_in[ly + kFirHalf][lx + kFirHalf];
-        if (out) out[static_cast<size_t>(orow + ly + out_r0) * out_pitch + ocol + lx + kPad] = v;
-        if (surf) surf2Dwrite(v, surf, (ocol + lx) * static_cast<int>(sizeof(float)), srow + orow + ly);
+        out[static_cast<size_t>(orow + ly + out_r0) * out_pitch + ocol + lx + kPad] = v;
       }
     }
     return;
@@ -237,8 +235,7 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
       if constexpr (QUAD) {
         s_in[sy + t][lx] = (gc >= 0 && gc < n_cols) ? acc : 0.f;  // s_in is free after the row pass
       } else if (gr < n_rows && gc < n_cols) {
-        if (out) out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = acc;
-        if (surf) surf2Dwrite(acc, surf, gc * static_cast<int>(sizeof(float)), srow + gr);
+        out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = acc;
       }
     }
   }
@@ -1028,10 +1025,10 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
   ImageSource isrc{image, p.N};
   if (p.img_quad && p.interp == 3)
     k_prefilter<ImageSource, true><<<dim3((p.img_pitch + kPfQuads - 1) / kPfQuads, (p.N + kPfRows - 1) / kPfRows, batch),
-                                     kThreads, 0, st>>>(p, isrc, p.N, p.N, nullptr, 0, 0, 0, 0, 0);
+                                     kThreads, 0, st>>>(p, isrc, p.N, p.N, nullptr, 0, 0, 0);
   else
     k_prefilter<ImageSource, false><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows, batch),
-                                      kThreads, 0, st>>>(p, isrc, p.N, p.N, p.coef_img, p.img_pitch, kPad, p.bs_img, 0, 0);
+                                      kThreads, 0, st>>>(p, isrc, p.N, p.N, p.coef_img, p.img_pitch, kPad, p.bs_img);
   hook(0, st);
   const dim3 sgrid((p.n_eanc + 1) / 2, (p.nh + kSampleWarps - 1) / kSampleWarps, p.M * batch);
   if (p.img_quad && p.interp == 3)
@@ -1053,8 +1050,7 @@ cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image
   hook(-1, st);
   SinoSource ssrc{sino, p.n_angles, p.n_det, p.live_lo, p.live_hi};
   k_prefilter<SinoSource, false><<<dim3((p.n_det + 1 + kPfCols - 1) / kPfCols, (p.n_angles + kPfRows - 1) / kPfRows, batch),
-                            kThreads, 0, st>>>(p, ssrc, p.n_angles, p.n_det + 1, p.coef_sino, p.sino_pitch, 0, p.bs_sino, 0,
-                                               0);
+                            kThreads, 0, st>>>(p, ssrc, p.n_angles, p.n_det + 1, p.coef_sino, p.sino_pitch, 0, p.bs_sino);
   hook(5, st);
   launch_rows_forward<true>(p, st, batch);
   hook(6, st);
