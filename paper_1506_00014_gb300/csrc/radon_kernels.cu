@@ -296,21 +296,6 @@ __device__ __forceinline__ float sample_image(const DevPlan& p, int b, int ic, f
 // Shared-memory layout of a forward row CTA (float2 units): bufA, bufB (nc each), the 16-byte
 // aligned anchor table (float4 per sub-angle and tile), the sub-angle directions, the twiddles.
 
-// Interpolant from the quad layout at padded index coordinates (ic + ac, ir + ar): one 16-byte
-// load per tap row.
-__device__ __forceinline__ float sample_image_quad(const DevPlan& p, int b, int ic, float ac, int ir, float ar) {
-  const float4* __restrict__ base = p.coef_q4 + b * p.bs_img + static_cast<size_t>(ir - 1) * p.img_pitch + (ic - 1);
-  float wc[4], wr[4];
-  bspline_w(ac, wc);
-  bspline_w(ar, wr);
-  float acc = 0.f;
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    const float4 v = __ldg(base + d * p.img_pitch);
-    acc = fmaf(wr[d], fmaf(wc[0], v.x, fmaf(wc[1], v.y, fmaf(wc[2], v.z, wc[3] * v.w))), acc);
-  }
-  return acc;
-}
 
 
 // Forward sampling (Algorithm 1: resample T_m f on Omega_lp, average the r sub-angles onto
@@ -319,17 +304,9 @@ __device__ __forceinline__ float sample_image_quad(const DevPlan& p, int b, int 
 // spectrum scratch yspec (free until the theta convolution), 2 x_pitch floats per row.
 constexpr int kSampleWarps = 8;
 
-// Cubic B-spline weights times 6 (the 1/36 of a 2-D tap block is applied once per output).
-__device__ __forceinline__ void bspline_w6(float a, float (&w)[4]) {
-  const float om = 1.f - a;
-  const float a2 = a * a;
-  w[0] = om * om * om;
-  w[1] = fmaf(a2, fmaf(3.f, a, -6.f), 4.f);
-  w[2] = fmaf(a, fmaf(a, fmaf(-3.f, a, 3.f), 3.f), 1.f);
-  w[3] = a2 * a;
-}
 
-// bspline_w6 for two fractions at once (.x and .y), with paired FP32 arithmetic.
+// Cubic B-spline weights times 6 (the 1/36 of a 2-D tap block is applied once per output) for
+// two fractions at once (.x and .y), with paired FP32 arithmetic.
 __device__ __forceinline__ void bspline_w6_pair(float2 a, float2 (&w)[4]) {
   const float2 one = make_float2(1.f, 1.f);
   const float2 om = __ffma2_rn(a, make_float2(-1.f, -1.f), one);
@@ -429,7 +406,38 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_sample_fwd(DevPlan p) {
 
 // Back-projection: G(phi_j, rho_i) = g~(phi_j + m beta, (e^rho_i - (1 - a_R) cos phi_j) / a_R).
 // The theta taps (rows of the extended sinogram, flips, weights) are the same for the whole row;
-// a flipped row (theta + pi) is read at k -> n_det - k, i.e. with reversed s weights.
+// a flipped row (theta + pi) is read at k -> n_det - k, i.e. with reversed s weights.  FLIPS:
+// 0 no tap row flipped, 1 all flipped, 2 mixed (the flags are uniform over the CTA, so the loop
+// is chosen once per row).
+template <int FLIPS>
+__device__ __forceinline__ void backproject_row_cubic(const DevPlan& p, const float* const (&rows)[4],
+                                                      const bool (&flip)[4], const float (&wt)[4], int cjx,
+                                                      float Fc, float* __restrict__ h) {
+  const int pitch = p.sino_pitch;
+  const int K = p.n_det + 2 * kPad;  // padded index of a flipped tap: K - c
+  for (int i = threadIdx.x; i < p.N_rho; i += blockDim.x) {
+    const int2 ei = p.bp_e[i];
+    const float F = __int_as_float(ei.y) + Fc;
+    const float fl = floorf(F);
+    const int is = ei.x + cjx + static_cast<int>(fl);
+    float ws[4];
+    bspline_w(F - fl, ws);
+    const int bf = FLIPS == 1 ? 0 : clampi(is - 1, 0, pitch - 4);      // forward taps is-1 .. is+2
+    const int bb = FLIPS == 0 ? 0 : clampi(K - is - 2, 0, pitch - 4);  // flipped taps K-is-2 .. K-is+1
+    float acc = 0.f;
+#pragma unroll
+    for (int dt = 0; dt < 4; ++dt) {
+      const bool fd = FLIPS == 2 ? flip[dt] : FLIPS == 1;
+      const float* r = rows[dt] + (fd ? bb : bf);
+      const float x0 = __ldg(r), x1 = __ldg(r + 1), x2 = __ldg(r + 2), x3 = __ldg(r + 3);
+      const float v = fd ? fmaf(ws[3], x0, fmaf(ws[2], x1, fmaf(ws[1], x2, ws[0] * x3)))
+                         : fmaf(ws[0], x0, fmaf(ws[1], x1, fmaf(ws[2], x2, ws[3] * x3)));
+      acc = fmaf(wt[dt], v, acc);
+    }
+    h[i] = acc;
+  }
+}
+
 __device__ void sample_row_backproject(const DevPlan& p, int b, int m, int jj, float* __restrict__ h) {
   const int2 th = p.bp_th[m * p.nh + jj];
   const int2 cj = p.bp_c[jj];
@@ -449,11 +457,22 @@ __device__ void sample_row_backproject(const DevPlan& p, int b, int m, int jj, f
     wt[2] = wt[3] = 0.f;
   }
   const int t0 = cubic ? th.x - 1 : th.x;
+  int nflip = 0;
   for (int dt = 0; dt < 4; ++dt) {
     int a2 = (t0 + dt) % (2 * na);
     if (a2 < 0) a2 += 2 * na;
     flip[dt] = a2 >= na;
+    nflip += (dt < ntap && flip[dt]) ? 1 : 0;
     rows[dt] = p.coef_sino + b * p.bs_sino + static_cast<size_t>(flip[dt] ? a2 - na : a2) * pitch;
+  }
+  if (cubic) {
+    if (nflip == 0)
+      backproject_row_cubic<0>(p, rows, flip, wt, cj.x, Fc, h);
+    else if (nflip == 4)
+      backproject_row_cubic<1>(p, rows, flip, wt, cj.x, Fc, h);
+    else
+      backproject_row_cubic<2>(p, rows, flip, wt, cj.x, Fc, h);
+    return;
   }
   for (int i = threadIdx.x; i < p.N_rho; i += blockDim.x) {
     const int2 ei = p.bp_e[i];
@@ -461,29 +480,14 @@ __device__ void sample_row_backproject(const DevPlan& p, int b, int m, int jj, f
     const float fl = floorf(F);
     const int is = ei.x + cj.x + static_cast<int>(fl);
     const float as = F - fl;
+    const int bf = clampi(is, 0, pitch - 2);
+    const int bb = clampi(K - is - 1, 0, pitch - 2);
     float acc = 0.f;
-    if (cubic) {
-      float ws[4];
-      bspline_w(as, ws);
-      const int bf = clampi(is - 1, 0, pitch - 4);       // forward taps is-1 .. is+2
-      const int bb = clampi(K - is - 2, 0, pitch - 4);   // flipped taps K-is-2 .. K-is+1
-#pragma unroll
-      for (int dt = 0; dt < 4; ++dt) {
-        const float* r = rows[dt] + (flip[dt] ? bb : bf);
-        const float x0 = __ldg(r), x1 = __ldg(r + 1), x2 = __ldg(r + 2), x3 = __ldg(r + 3);
-        const float v = flip[dt] ? fmaf(ws[3], x0, fmaf(ws[2], x1, fmaf(ws[1], x2, ws[0] * x3)))
-                                 : fmaf(ws[0], x0, fmaf(ws[1], x1, fmaf(ws[2], x2, ws[3] * x3)));
-        acc = fmaf(wt[dt], v, acc);
-      }
-    } else {
-      const int bf = clampi(is, 0, pitch - 2);
-      const int bb = clampi(K - is - 1, 0, pitch - 2);
-      for (int dt = 0; dt < ntap; ++dt) {
-        const float* r = rows[dt] + (flip[dt] ? bb : bf);
-        const float x0 = __ldg(r), x1 = __ldg(r + 1);
-        const float v = flip[dt] ? fmaf(as, x0 - x1, x1) : fmaf(as, x1 - x0, x0);
-        acc = fmaf(wt[dt], v, acc);
-      }
+    for (int dt = 0; dt < ntap; ++dt) {
+      const float* r = rows[dt] + (flip[dt] ? bb : bf);
+      const float x0 = __ldg(r), x1 = __ldg(r + 1);
+      const float v = flip[dt] ? fmaf(as, x0 - x1, x1) : fmaf(as, x1 - x0, x0);
+      acc = fmaf(wt[dt], v, acc);
     }
     h[i] = acc;
   }

@@ -185,6 +185,29 @@ def test_host_buffer_entry_points_match_device_ones(rl):
     assert np.array_equal(hi.astype(np.float64), _gpu_back(rl, plan, g))
 
 
+def test_concurrent_plans_on_two_streams_match_serial(rl):
+    """R with one plan and R# with another, on two streams at once (how the benchmark runs a step),
+    give the same bits as running them one after the other."""
+    N, na, nd = 256, 384, 384
+    p1 = rl.radon_plan_create(N, na, nd, 3, 3)
+    p2 = rl.radon_plan_create(N, na, nd, 3, 3)
+    f = torch.tensor(ellipse_image(N, random_ellipses(20, 8)).astype(np.float32), device="cuda")
+    g = torch.tensor(random_sinogram(na, nd, 9).astype(np.float32), device="cuda")
+    s_ref = torch.empty((na, nd), device="cuda")
+    i_ref = torch.empty((N, N), device="cuda")
+    rl.radon_forward(p1, f, s_ref)
+    rl.radon_backproject(p1, g, i_ref)
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    s, i = torch.empty_like(s_ref), torch.empty_like(i_ref)
+    for _ in range(3):
+        side.wait_stream(main)
+        rl.radon_forward(p1, f, s, main)
+        rl.radon_backproject(p2, g, i, side)
+        main.wait_stream(side)
+    torch.cuda.synchronize()
+    assert torch.equal(s, s_ref) and torch.equal(i, i_ref)
+
+
 def test_kernel_launch_counts(rl):
     plan = rl.radon_plan_create(64, 64, 96, 3, 3)
     assert rl.radon_plan_kernel_launches(plan, "forward") == 6
