@@ -56,6 +56,29 @@ def test_autograd_gradients_pass_finite_differences_on_smooth_inputs(rl):
     assert float((grad2 * G).sum()) == pytest.approx(float(fd2), rel=2e-4)
 
 
+def test_dot_product_identity_on_smooth_inputs(rl):
+    """<R f, g> = c_R <f, R# g> (the adjoint relation the autograd backward relies on, c_R =
+    dx^2 / (dtheta ds)) for smooth f and g; R# is the discretised continuous adjoint, so the
+    identity holds to the method's accuracy, not to rounding."""
+    from paper_1506_00014_gb300.autograd import adjoint_scales
+
+    N, na, nd = 256, 384, 384
+    plan = rl.radon_plan_create(N, na, nd, 3, 3)
+    geo = geometry.make_geometry(N, na, nd, 3)
+    th = np.arange(na) * geo.dtheta
+    s = (np.arange(nd) - nd / 2) * geo.ds
+    f = _t(gaussian_image(N, BLOBS))
+    g = _t(direct.gaussian_radon(th[:, None], s[None, :], BLOBS2))
+    rf = torch.empty((na, nd), device="cuda")
+    bg = torch.empty((N, N), device="cuda")
+    rl.radon_forward(plan, f, rf)
+    rl.radon_backproject(plan, g, bg)
+    c_r, _ = adjoint_scales(plan)
+    lhs = float((rf.double() * g.double()).sum())
+    rhs = c_r * float((f.double() * bg.double()).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-4)
+
+
 def test_batched_autograd_equals_per_slice(rl):
     from paper_1506_00014_gb300.autograd import radon
 
