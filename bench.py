@@ -267,19 +267,24 @@ def bench_fbp_large(rl, torch, flush) -> dict:
             "accuracy": "closed form (FBP of analytic Gaussians) checked in tests/test_gpu_parity.py"}
 
 
-def _dram_traffic() -> dict:
-    """Per-launch DRAM bytes by stage from the committed ncu summary (empty if absent)."""
+def _ncu_summary() -> dict:
+    """Per stage (DRAM bytes per launch, L1/TEX %, issue %) from the committed ncu summary."""
     out = {}
     path = os.path.join(ROOT, "profiles", "dram_traffic_radon_pair_N2048.txt")
     try:
         with open(path) as fh:
             for line in fh:
                 parts = line.split()
-                if len(parts) == 2 and not line.startswith("#"):
-                    out[parts[0]] = float(parts[1])
+                if len(parts) == 4 and not line.startswith("#"):
+                    out[parts[0]] = tuple(float(x) for x in parts[1:])
     except OSError:
         pass
     return out
+
+
+def _dram_traffic() -> dict:
+    """Per-launch DRAM bytes by stage from the committed ncu summary (empty if absent)."""
+    return {k: v[0] for k, v in _ncu_summary().items()}
 
 
 def reduce_max(value: float, dist, device) -> float:
@@ -404,6 +409,7 @@ def run_ours(args):
     achieved = nbytes[dom] / (dom_ms / 1e3) / 1e9
     stage_ms = {k: round(v[0] / max(1, v[1]), 4) for k, v in stage.items()}
     traffic = _dram_traffic().get(dom)
+    summary = _ncu_summary().get(dom)
 
     # the linear-interpolation variant of the same workload (same timing rules, fewer steps)
     plan_lin = rl.radon_plan_create(N, N_ANGLES, N_DET, 1, M)
@@ -497,6 +503,10 @@ def run_ours(args):
             "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes": nbytes[dom], "ms_per_launch": dom_ms,
+            "binding_units_ncu": None if summary is None else {
+                "l1tex_pct_of_peak": summary[1], "issue_pct_of_peak": summary[2],
+                "note": "not HBM-bound: the kernel is limited by L1/TEX and instruction issue "
+                        "(profiles/kernels_radon_pair_N2048.md)"},
         },
         "cpu_baseline": cpu,
         "err_vs_oracle": err,
