@@ -106,8 +106,8 @@ int radon_fbp(radon_plan plan, const float* d_sino, float* d_image, int filter, 
  * the device (call it before any stream capture).  It returns RADON_NOT_SUPPORTED when the
  * stacked slices exceed the device's 2-D surface height.  radon_forward_batch /
  * radon_backproject_batch then transform `batch` <= max_batch slices stored back to back
- * ([batch][N][N] images, [batch][n_angles][n_det] sinograms) with the same five kernel launches
- * as one slice; results equal those of per-slice calls. */
+ * ([batch][N][N] images, [batch][n_angles][n_det] sinograms) with the same kernel launches as
+ * one slice (radon_plan_kernel_launches); results equal those of per-slice calls. */
 int radon_plan_reserve_batch(radon_plan plan, int max_batch);
 int radon_forward_batch(radon_plan plan, const float* d_images, float* d_sinos, int batch, void* stream);
 int radon_backproject_batch(radon_plan plan, const float* d_sinos, float* d_images, int batch, void* stream);

@@ -1,10 +1,10 @@
 """Many slices of uneven sizes (Section 7 batches slices "to fill up the GPU memory").
 
 Slices are grouped by size.  Each group runs as same-size batches of at most the plan's batch
-capacity (one set of five launches per transform and batch: radon_forward_batch /
+capacity (one set of launches per transform and batch: radon_forward_batch /
 radon_backproject_batch), and the whole multi-size sequence can be captured once in a CUDA graph
-and replayed.  `tune()` picks, per plan, the column-group size of the theta convolution by
-timing; that knob does not change results.
+and replayed.  `tune()` picks, per plan, the slices per batched call and the theta-convolution
+kernel by timing; neither changes results beyond FP32 rounding.
 """
 
 from __future__ import annotations

@@ -284,17 +284,15 @@ __device__ __forceinline__ float sample_image(const DevPlan& p, int b, int ic, f
 // Forward: h(phi_j, rho_i) = e^rho_i / r * sum_q f~(T_m^{-1}(e^rho_i (cos phi_jq, sin phi_jq))).
 //
 // Coordinates: for each sub-angle q and each 32-sample rho tile, a double-float anchor
-// col/row = e^rho_anchor * (cos, sin)(psi_q) * N / (2 a_R) + offset, computed once per CTA into
+// col/row = e^rho_anchor * (cos, sin)(psi_q) * N / (2 a_R) + offset, computed once per warp into
 // shared memory as (integer, fraction); each sample adds the FP32 offset (e^rho_i - e^rho_anchor)
 // times the direction.
 //
 // Taps: with img_quad each of the 4 tap rows is one aligned 16-byte load from the quad layout;
-// otherwise 16 scalar loads from the padded coefficient image.  Samples more than kDiscMargin
-// pixels outside the unit disc are skipped: the pre-filtered disc-masked image decays like
+// otherwise 16 scalar loads from the padded coefficient image.  Samples whose tap block lies
+// farther than kDiscMargin pixels outside the unit disc (or outside the padded array) are skipped
+// through the host's per-sub-angle rho ranges: the pre-filtered disc-masked image decays like
 // 0.27^d away from the disc, below 1e-8 of its maximum there.
-
-// Shared-memory layout of a forward row CTA (float2 units): bufA, bufB (nc each), the 16-byte
-// aligned anchor table (float4 per sub-angle and tile), the sub-angle directions, the twiddles.
 
 
 
