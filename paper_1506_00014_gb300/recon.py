@@ -163,3 +163,32 @@ class BatchedLeastSquares:
         with torch.no_grad():
             r = self._radon(self.f.detach(), self.plan) - self.g
             return (r * r).sum(dim=(1, 2))
+
+
+def em_batched(plan: binding.RadonPlan, g: torch.Tensor, iters: int, eps: float = 1e-12) -> torch.Tensor:
+    """em() for a stack of slices g [B, n_angles, n_det] (a volume): every R and R# goes through
+    the batched C ABI in chunks of the plan's reserved capacity, and everything stays on the GPU
+    between the upload of g and the returned stack f [B, N, N]."""
+    info = plan.info
+    nd, na = info["n_det"], info["n_angles"]
+    B = g.shape[0]
+    cap = max(1, getattr(plan, "max_batch", 1))
+    k = torch.arange(nd, device="cuda")
+    chi = (2 * (2 * k - nd) ** 2 < nd * nd).to(torch.float32).expand(na, nd).contiguous()
+    norm = torch.empty(plan.image_shape, device="cuda")
+    _bp(plan, chi, norm)
+    disc = norm > eps
+    f = torch.where(disc, 1.0, 0.0).to(torch.float32).expand(B, *plan.image_shape).contiguous()
+    r = torch.empty((B,) + plan.sino_shape, device="cuda")
+    back = torch.empty_like(f)
+    g = g.contiguous()
+    for _ in range(iters):
+        for b0 in range(0, B, cap):
+            b1 = min(B, b0 + cap)
+            binding.radon_forward_batch(plan, f[b0:b1], r[b0:b1])
+        ratio = torch.where(r > eps, g / r.clamp_min(eps), torch.zeros_like(r)) * chi
+        for b0 in range(0, B, cap):
+            b1 = min(B, b0 + cap)
+            binding.radon_backproject_batch(plan, ratio[b0:b1].contiguous(), back[b0:b1])
+        f = torch.where(disc, f * back / norm.clamp_min(eps), torch.zeros_like(f))
+    return f

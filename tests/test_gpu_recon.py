@@ -182,3 +182,20 @@ def test_em_keeps_positivity_and_fits_the_data(rl):
         return float(torch.linalg.norm(s - g) / torch.linalg.norm(g))
 
     assert resid(f30) < resid(f5) < 1.0
+
+
+def test_batched_em_on_a_slice_stack_equals_per_slice(rl):
+    """em_batched (batched C ABI over a stack of slices) gives each slice the same bits as em()."""
+    from paper_1506_00014_gb300.recon import em, em_batched
+
+    N, na, nd = 64, 96, 64
+    plan = rl.radon_plan_create(N, na, nd, 3, 3)
+    rl.radon_plan_reserve_batch(plan, 2)
+    stack = []
+    for b in range(3):
+        ell = [type(e)(e.cx, e.cy, e.a, e.b, e.psi, abs(e.density)) for e in random_ellipses(6, 50 + b)]
+        stack.append(_t(ellipse_sinogram(ell, na, nd)))
+    g = torch.stack(stack)
+    got = em_batched(plan, g, 8)
+    for b in range(3):
+        assert torch.equal(got[b], em(plan, stack[b], 8))
