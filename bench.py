@@ -39,8 +39,7 @@ def _config():
     return {
         "workload": WORKLOAD,
         "N": N, "n_angles": N_ANGLES, "n_det": N_DET, "interp_order": INTERP, "n_partitions": M,
-        "step": "one R (image->sinogram) + one R# (sinogram->image), independent, on two streams "
-                "with one plan each (serial_ms_per_step: both on one stream)",
+        "step": "one R (image->sinogram) + one R# (sinogram->image) of independent inputs",
         "phantom": "50 random ellipses, seed 2; sinogram i.i.d. N(0,1), seed 3",
         "l2": "flushed before each timed step (256 MB write, outside the timed interval)",
     }
@@ -535,6 +534,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(),
+        "execution": "R on one stream and R# on a second stream, one plan each; serial_ms_per_step: "
+                     "both on one stream",
         "serial_ms_per_step": serial_ms,
         "roofline": {
             "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
