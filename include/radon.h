@@ -74,7 +74,11 @@ typedef struct {
  * (cubic B-spline); n_partitions M >= 3.  Computes the geometry and the kernel transforms
  * zeta_hat / B_hat, zeta#_hat / B_hat in FP64 on the host (trapezoid rule with the end
  * corrections of Eq. weightsa), uploads them as FP32 and allocates the scratch buffers on the
- * current device.  Synchronous.  *out is set to NULL on failure. */
+ * current device.  Synchronous.  *out is set to NULL on failure.  Returns RADON_INVALID_ARG for
+ * arguments outside these ranges and RADON_NOT_SUPPORTED for valid sizes this build cannot hold:
+ * one rho row (N_rho / 2 complex values, about 1.07 N) or one theta column group must fit in a
+ * CTA's shared memory, which limits N to about 8700 and n_angles to about 14000 with
+ * M = 3. */
 int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int interp_order,
                       int n_partitions);
 
