@@ -115,6 +115,14 @@ struct ImageSource {
     const unsigned d2 = static_cast<unsigned>(dr * dr) + static_cast<unsigned>(dc * dc);
     return d2 < static_cast<unsigned>(N) * static_cast<unsigned>(N) ? __ldg(f + static_cast<size_t>(r) * N + c) : 0.f;
   }
+  // True when every input of the window [r0, r1) x [c0, c1) is zero: the window lies inside the
+  // array (no boundary extension) and its pixel nearest the centre is outside the disc (convex).
+  __device__ __forceinline__ bool dead(int r0, int r1, int c0, int c1) const {
+    if (!interior(r0, r1, c0, c1)) return false;
+    const int r = min(max(N / 2, r0), r1 - 1), c = min(max(N / 2, c0), c1 - 1);
+    const int dr = 2 * r - N, dc = 2 * c - N;
+    return static_cast<unsigned>(dr * dr) + static_cast<unsigned>(dc * dc) >= static_cast<unsigned>(N) * static_cast<unsigned>(N);
+  }
   __device__ __forceinline__ float extended(int r, int c) const {
     float sr, sc;
     const int rr = odd_ext(r, N, &sr);
@@ -135,6 +143,11 @@ struct SinoSource {
   }
   __device__ __forceinline__ float direct(int a, int k) const {
     return (k >= live_lo && k <= live_hi) ? __ldg(g + static_cast<size_t>(a) * nd + k) : 0.f;
+  }
+  // True when every input of the window is zero: its bins lie inside [0, n_det] (no s extension)
+  // and miss the live range; theta rows (periodic, flipped k -> n_det - k) keep the live set.
+  __device__ __forceinline__ bool dead(int, int, int c0, int c1) const {
+    return c0 >= 0 && c1 <= nd + 1 && (c1 <= live_lo || c0 > live_hi);
   }
   __device__ __forceinline__ float extended(int r, int c) const {
     int a2 = r % (2 * na);
@@ -167,6 +180,25 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
   const int ccol = QUAD ? qcol - 3 : blockIdx.x * kPfCols;      // first coefficient column computed
   const int r0 = blockIdx.y * kPfRows - kFirHalf, c0 = ccol - kFirHalf;
   const int tid = threadIdx.x;
+  if (src.dead(r0, r0 + kPfInR, c0, c0 + kPfInC)) {  // all coefficients of the tile are zero
+    const int orow = blockIdx.y * kPfRows;
+    if constexpr (QUAD) {
+      const int P = p.img_pitch;
+      float4* q4 = p.coef_q4 + b * p.bs_img;
+      for (int idx = tid; idx < kPfRows * kPfQuads; idx += kThreads) {
+        const int y = idx / kPfQuads, lx = idx - y * kPfQuads;
+        const int gr = orow + y, c = qcol + lx;
+        if (gr < n_rows && c < P) q4[static_cast<size_t>(gr + kPad) * P + c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+      for (int idx = tid; idx < kPfRows * kPfCols; idx += kThreads) {
+        const int y = idx / kPfCols, lx = idx - y * kPfCols;
+        const int gr = orow + y, gc = ccol + lx;
+        if (gr < n_rows && gc < n_cols) out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = 0.f;
+      }
+    }
+    return;
+  }
   if (src.interior(r0, r0 + kPfInR, c0, c0 + kPfInC)) {
     // all loads of this thread are issued before the first shared-memory store
     constexpr int kPer = (kPfInR * kPfInC + kThreads - 1) / kThreads;
