@@ -301,6 +301,29 @@ def bench_em_volume(rl, torch, n: int = 256, iters: int = 100) -> dict:
             "paper_gtx770_seconds": {"256": 88.0, "512": 690.0, "1024": 5400.0, "2048": 42000.0}.get(str(n))}
 
 
+def bench_paper_table1(rl, torch, flush) -> dict:
+    """R# per slice on the paper's own back-projection workload (Table 1): N x N images from
+    1.5 N angles x N bins, M = 3, slices batched (the paper batched slices to fill GPU memory).
+    Seeded N(0, 1) sinograms; the work does not depend on the values."""
+    paper = {256: 1.6e-3, 512: 6.1e-3, 1024: 2.5e-2, 2048: 9.9e-2}  # seconds, GTX 770
+    out = {}
+    for n, batch in ((256, 32), (512, 16), (1024, 8), (2048, 4)):
+        na, nd = 3 * n // 2, n
+        plan = rl.radon_plan_create(n, na, nd, 3, 3)
+        rl.radon_plan_reserve_batch(plan, batch)
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        g = torch.randn((batch, na, nd), device="cuda", generator=gen)
+        img = torch.empty((batch, n, n), device="cuda")
+        fn = lambda: rl.radon_backproject_batch(plan, g, img)  # noqa: E731
+        for _ in range(2):
+            fn()
+        t = _event_ms(torch, fn, 5, flush) / batch
+        out[str(n)] = {"n_angles": na, "n_det": nd, "batch": batch, "ms_per_slice": t,
+                       "paper_gtx770_ms_per_slice": 1e3 * paper[n]}
+        del plan, g, img
+    return out
+
+
 def _ncu_summary() -> dict:
     """Per stage (DRAM bytes per launch, L1/TEX %, issue %) from the committed ncu summary."""
     out = {}
@@ -515,6 +538,7 @@ def run_ours(args):
         extras["batched"] = bench_batched(rl, torch, flush)
         extras["least_squares"] = bench_least_squares(rl, torch)
         extras["fbp_8192"] = bench_fbp_large(rl, torch, flush)
+        extras["paper_table1_backprojection"] = bench_paper_table1(rl, torch, flush)
         extras["em_volume_256"] = bench_em_volume(rl, torch, 256)
         extras["em_volume_512"] = bench_em_volume(rl, torch, 512)
 
