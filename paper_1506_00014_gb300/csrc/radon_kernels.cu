@@ -869,7 +869,7 @@ __global__ void __launch_bounds__(128) k_gather_sino(DevPlan p, float* __restric
 }
 
 // R# g(x) = sum_m interpolant of partition m at the log-polar coordinates of T_m x.
-__global__ void __launch_bounds__(kPTile * kPTile) k_gather_image(DevPlan p, float* __restrict__ img) {
+__global__ void __launch_bounds__(kPTile * kPTile, 6) k_gather_image(DevPlan p, float* __restrict__ img) {
   const int N = p.N;
   const int tj = blockIdx.x, ti = blockIdx.y, b = blockIdx.z;
   img += static_cast<size_t>(b) * N * N;
