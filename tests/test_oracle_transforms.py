@@ -65,6 +65,37 @@ def test_direct_radon_of_one_basis_function():
         assert R[a, kk] == pytest.approx(ref, abs=1e-9)
 
 
+def test_direct_radon_obeys_the_fourier_slice_theorem():
+    """For the spline f~(x) = sum_ij c_ij B((x1 - x_j)/h) B((x2 - x_i)/h), h = 2/N, the 2-D Fourier
+    transform is h^2 sinc^4(h xi1) sinc^4(h xi2) sum_ij c_ij exp(-2 pi i (xi1 x_j + xi2 x_i)), and
+    int R f(theta, s) exp(-2 pi i sigma s) ds equals it at xi = sigma (cos theta, sin theta)
+    (Fourier slice theorem).  The s integral is the sum over the detector grid (f~ is smooth and
+    compactly supported, so the sum is accurate far below the tolerance).  Pins orientation, sign,
+    scale and the interpolant model of the direct oracle, independently of its prefilter."""
+    N = 32
+    h = 2.0 / N
+    geo = geometry.make_geometry(N, 12, 192, 3)
+    x = (np.arange(N) - N / 2) * h
+    X1, X2 = np.meshgrid(x, x)  # X1[i, j] = x_j (column), X2[i, j] = x_i (row)
+    r2 = (X1 - 0.1) ** 2 + (X2 + 0.05) ** 2
+    c = np.where(np.hypot(X1, X2) < 0.75, np.exp(-r2 / (2 * 0.12 ** 2)), 0.0)
+    # image samples of the spline: [1, 4, 1] / 6 along both axes (zero outside the array)
+    k3 = np.array([1.0, 4.0, 1.0]) / 6.0
+    f = np.apply_along_axis(lambda v: np.convolve(v, k3, mode="same"), 0, c)
+    f = np.apply_along_axis(lambda v: np.convolve(v, k3, mode="same"), 1, f)
+    R = direct.radon_direct(f, geo)
+    s = (np.arange(geo.n_det) - geo.n_det / 2) * geo.ds
+    F0 = h * h * c.sum()
+    for a in (0, 3, 7, 10):
+        th = a * geo.dtheta
+        for sigma in (0.7, 2.3, 5.1):
+            num = geo.ds * np.sum(R[a] * np.exp(-2j * np.pi * sigma * s))
+            xi1, xi2 = sigma * math.cos(th), sigma * math.sin(th)
+            F = h * h * np.sinc(h * xi1) ** 4 * np.sinc(h * xi2) ** 4 * np.sum(
+                c * np.exp(-2j * np.pi * (xi1 * X1 + xi2 * X2)))
+            assert abs(num - F) < 1e-9 * abs(F0), (a, sigma, num, F)
+
+
 def test_direct_radon_converges_to_analytic_gaussian():
     errs = []
     for N in (32, 64):
