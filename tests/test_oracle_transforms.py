@@ -69,8 +69,10 @@ def test_direct_radon_obeys_the_fourier_slice_theorem():
     """For the spline f~(x) = sum_ij c_ij B((x1 - x_j)/h) B((x2 - x_i)/h), h = 2/N, the 2-D Fourier
     transform is h^2 sinc^4(h xi1) sinc^4(h xi2) sum_ij c_ij exp(-2 pi i (xi1 x_j + xi2 x_i)), and
     int R f(theta, s) exp(-2 pi i sigma s) ds equals it at xi = sigma (cos theta, sin theta)
-    (Fourier slice theorem).  The s integral is the sum over the detector grid (f~ is smooth and
-    compactly supported, so the sum is accurate far below the tolerance).  Pins orientation, sign,
+    (Fourier slice theorem).  The s integral is the sum over the detector grid: f~ is compactly
+    supported, and the sum is accurate to ~2e-7 of F(0) at theta = 0 (where R f(0, .) is itself a
+    spline with knots every pixel, whose aliased spectrum the sum picks up) and ~1e-10 elsewhere;
+    a transposed or sign-flipped convention misses by more than 0.5.  Pins orientation, sign,
     scale and the interpolant model of the direct oracle, independently of its prefilter."""
     N = 32
     h = 2.0 / N
@@ -93,7 +95,7 @@ def test_direct_radon_obeys_the_fourier_slice_theorem():
             xi1, xi2 = sigma * math.cos(th), sigma * math.sin(th)
             F = h * h * np.sinc(h * xi1) ** 4 * np.sinc(h * xi2) ** 4 * np.sum(
                 c * np.exp(-2j * np.pi * (xi1 * X1 + xi2 * X2)))
-            assert abs(num - F) < 1e-9 * abs(F0), (a, sigma, num, F)
+            assert abs(num - F) < 1e-6 * abs(F0), (a, sigma, num, F)
 
 
 def test_direct_radon_converges_to_analytic_gaussian():
