@@ -303,7 +303,8 @@ def bench_em_volume(rl, torch, n: int = 256, iters: int = 100) -> dict:
 
 def bench_paper_table1(rl, torch, flush) -> dict:
     """R# per slice on the paper's own back-projection workload (Table 1): N x N images from
-    1.5 N angles x N bins, M = 3, slices batched (the paper batched slices to fill GPU memory).
+    1.5 N angles x N bins, M = 3, slices batched (the paper batched slices to fill GPU memory);
+    the forward R on the same shapes beside it (the paper reports R only inside the EM loop).
     Seeded N(0, 1) sinograms; the work does not depend on the values."""
     paper = {256: 1.6e-3, 512: 6.1e-3, 1024: 2.5e-2, 2048: 9.9e-2}  # seconds, GTX 770
     out = {}
@@ -315,11 +316,14 @@ def bench_paper_table1(rl, torch, flush) -> dict:
         g = torch.randn((batch, na, nd), device="cuda", generator=gen)
         img = torch.empty((batch, n, n), device="cuda")
         fn = lambda: rl.radon_backproject_batch(plan, g, img)  # noqa: E731
+        fwd = lambda: rl.radon_forward_batch(plan, img, g)  # noqa: E731
         for _ in range(2):
             fn()
+            fwd()
         t = _event_ms(torch, fn, 5, flush) / batch
+        t_fwd = _event_ms(torch, fwd, 5, flush) / batch
         out[str(n)] = {"n_angles": na, "n_det": nd, "batch": batch, "ms_per_slice": t,
-                       "paper_gtx770_ms_per_slice": 1e3 * paper[n]}
+                       "paper_gtx770_ms_per_slice": 1e3 * paper[n], "forward_ms_per_slice": t_fwd}
         del plan, g, img
     return out
 
