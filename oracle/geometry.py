@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Conventions (readings of the paper, listed in the design doc):
+Conventions (readings of the paper where it is silent, ambiguous or garbled):
 
 * Image grid X (Eq. Xgrid, rescaled to the unit disc): pixel (i, j) of an
   N x N array has centre x1 = (j - N/2) * 2/N, x2 = (i - N/2) * 2/N.
