@@ -161,6 +161,27 @@ struct SinoSource {
   }
 };
 
+// Pre-filter of one segment: the kPfSeg coefficients at the centre of a window of kPfSeg +
+// 2 kFirHalf samples, by the recursion of Eq. Qfrecursive run inside the window: causal
+// u[k] = w[k] + z u[k-1] from zero state at the window start, anticausal v[k] = u[k] + z v[k+1]
+// from zero state at the window end, c = -6 z v (the pair's impulse response is
+// -6 z / (1 - z^2) z^|n| = sqrt(3) z^|n|).  The zero states sit kFirHalf samples outside the
+// segment, so the response is cut at the same z^15 as the truncated FIR; 8 operations per
+// coefficient instead of 29.
+__device__ __forceinline__ void segment_prefilter(float (&w)[kPfSeg + 2 * kFirHalf], float (&c)[kPfSeg]) {
+  constexpr float z = -0.267949192431122706f;  // sqrt(3) - 2
+  constexpr float g = -6.f * z;
+  constexpr int W = kPfSeg + 2 * kFirHalf;
+#pragma unroll
+  for (int k = 1; k < W; ++k) w[k] = fmaf(z, w[k - 1], w[k]);
+  float v = w[W - 1];
+#pragma unroll
+  for (int k = W - 2; k >= kFirHalf; --k) {
+    v = fmaf(z, v, w[k]);
+    if (k < kFirHalf + kPfSeg) c[k - kFirHalf] = g * v;
+  }
+}
+
 // QUAD: the tile's output is the quad-row layout coef_q4 (element (r, c) = padded coefficients
 // (r, c .. c+3), zero outside the image): kPfQuads quad origins per tile need the 64 coefficient
 // columns starting 3 to their left, which the tile computes as usual and then regroups in shared
@@ -233,22 +254,16 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
     }
     return;
   }
-  float q[kFirHalf + 1];
-#pragma unroll
-  for (int n = 0; n <= kFirHalf; ++n) q[n] = __ldg(p.fir + n);
   // along rows: kPfInR rows x (kPfCols / kPfSeg) segments
   for (int task = tid; task < kPfInR * (kPfCols / kPfSeg); task += kThreads) {
     const int ly = task / (kPfCols / kPfSeg), sx = (task - ly * (kPfCols / kPfSeg)) * kPfSeg;
     float w[kPfSeg + 2 * kFirHalf];
 #pragma unroll
     for (int t = 0; t < kPfSeg + 2 * kFirHalf; ++t) w[t] = s_in[ly][sx + t];
+    float c[kPfSeg];
+    segment_prefilter(w, c);
 #pragma unroll
-    for (int t = 0; t < kPfSeg; ++t) {
-      float acc = q[0] * w[t + kFirHalf];
-#pragma unroll
-      for (int n = 1; n <= kFirHalf; ++n) acc = fmaf(q[n], w[t + kFirHalf - n] + w[t + kFirHalf + n], acc);
-      s_mid[ly][sx + t] = acc;
-    }
+    for (int t = 0; t < kPfSeg; ++t) s_mid[ly][sx + t] = c[t];
   }
   __syncthreads();
   // along columns: kPfCols columns x (kPfRows / kPfSeg) segments
@@ -258,11 +273,11 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
 #pragma unroll
     for (int t = 0; t < kPfSeg + 2 * kFirHalf; ++t) w[t] = s_mid[sy + t][lx];
     const int gc = ocol + lx;
+    float c[kPfSeg];
+    segment_prefilter(w, c);
 #pragma unroll
     for (int t = 0; t < kPfSeg; ++t) {
-      float acc = q[0] * w[t + kFirHalf];
-#pragma unroll
-      for (int n = 1; n <= kFirHalf; ++n) acc = fmaf(q[n], w[t + kFirHalf - n] + w[t + kFirHalf + n], acc);
+      const float acc = c[t];
       const int gr = orow + sy + t;
       if constexpr (QUAD) {
         s_in[sy + t][lx] = (gc >= 0 && gc < n_cols) ? acc : 0.f;  // s_in is free after the row pass
