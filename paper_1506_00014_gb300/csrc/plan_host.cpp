@@ -494,11 +494,6 @@ int build_tables(const radon_plan_info& g, HostTables* t) {
     }
   }
 
-  // Truncated pre-filter: (Q f)_k = sum_n sqrt(3) z^|n| f_{k+n}, the impulse response of the
-  // recursion of Eq. Qfrecursive (z = sqrt(3) - 2), cut at |n| <= kFirHalf.
-  t->fir.resize(kFirHalf + 1);
-  const double z = std::sqrt(3.0) - 2.0;
-  for (int n = 0; n <= kFirHalf; ++n) t->fir[n] = static_cast<float>(std::sqrt(3.0) * std::pow(z, n));
   return RADON_OK;
 }
 

@@ -20,7 +20,7 @@ constexpr int kETile = 32;   // rho samples per coordinate anchor (forward log-p
 constexpr int kHaloLo = 2;   // output rows kept below the centre half of the angular grid
 constexpr int kHaloHi = 2;   // and above it (cubic taps of |phi| <= beta/2)
 constexpr int kPad = 3;      // zero border around the coefficient arrays (cubic taps never leave it)
-constexpr int kFirHalf = 14; // one-sided length of the truncated pre-filter (|z|^15 ~ 2.7e-9)
+constexpr int kFirHalf = 14; // pre-filter halo: recursions start this far outside a segment (|z|^15 ~ 2.7e-9)
 constexpr int kDiscMargin = 16;  // forward sampling skips fine samples farther than this many
                                  // pixels outside the disc (coefficients there are below 1e-9)
 
@@ -96,7 +96,6 @@ struct HostTables {
   // back-projection output (Algorithm 2: resample to X and sum the partitions)
   std::vector<int32_t> bp_anc;   // 8 per (m, tile): I_theta, F_theta, I_rho, F_rho, y0x, y0y, 1/|y0|^2, 0
   std::vector<float> bp_m;       // 2 per m: a_R cos(m beta), a_R sin(m beta)
-  std::vector<float> fir;        // kFirHalf + 1 pre-filter taps sqrt(3) z^n
   // FBP filter along s: real FFT of length n_filter (complex length n_filter / 2)
   Radices rad_filt;
   std::vector<float> tw_filt;     // 2 * (n_filter/2): exp(-2 pi i p / (n_filter/2))

@@ -333,7 +333,7 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   const size_t o_frng = tp.add(t.fwd_rng);
   const size_t o_fang = tp.add(t.fwd_ang), o_fanc = tp.add(t.fwd_anc);
   const size_t o_bth = tp.add(t.bp_th), o_bc = tp.add(t.bp_c), o_be = tp.add(t.bp_e);
-  const size_t o_banc = tp.add(t.bp_anc), o_bm = tp.add(t.bp_m), o_fir = tp.add(t.fir);
+  const size_t o_banc = tp.add(t.bp_anc), o_bm = tp.add(t.bp_m);
   const size_t o_twf = tp.add(t.tw_filt), o_twfr = tp.add(t.tw_filt_r2c), o_filt = tp.add(t.filt);
 
   cudaError_t e = cudaMalloc(&p->table_mem, tp.total());
@@ -362,7 +362,6 @@ int radon_plan_create(radon_plan* out, int N, int n_angles, int n_det, int inter
   d.bp_e = reinterpret_cast<const int2*>(tb + o_be);
   d.bp_anc = reinterpret_cast<const int4*>(tb + o_banc);
   d.bp_m = reinterpret_cast<const float2*>(tb + o_bm);
-  d.fir = reinterpret_cast<const float*>(tb + o_fir);
   d.tw_filt = reinterpret_cast<const float2*>(tb + o_twf);
   d.tw_filt_r2c = reinterpret_cast<const float2*>(tb + o_twfr);
   d.filt = reinterpret_cast<const float*>(tb + o_filt);

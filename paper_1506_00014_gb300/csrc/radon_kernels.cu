@@ -1,12 +1,14 @@
 // CUDA kernels of the log-polar Radon transform (Algorithm 1) and back-projection (Algorithm 2).
 //
 // Pipeline of one transform (one launch each, all on the caller's stream):
-//   prefilter  : B-spline coefficients Q f (Eq. Qfrecursive) as a truncated symmetric FIR
-//                (the impulse response sqrt(3) z^|n| of the recursion), disc / |s| < 1 masks.
-//   rows_fwd   : one CTA per angular row (m, j) of the log-polar grid: samples the row
-//                (Algorithm 1: T_m f on Omega_lp, box-averaged to Omega_p, times e^rho;
-//                 Algorithm 2: g(S_m) on Omega_p) into shared memory and applies the real FFT
-//                along rho; writes the half spectrum.
+//   prefilter  : B-spline coefficients Q f (Eq. Qfrecursive): the recursion run inside each
+//                thread's window of samples (response sqrt(3) z^|n| cut at |n| <= kFirHalf),
+//                disc / |s| < 1 masks; for cubic images the quad-row layout.
+//   sample_fwd : Algorithm 1's resampling of T_m f on Omega_lp, box-averaged to Omega_p, times
+//                e^rho, into the spectrum scratch.
+//   rows_fwd   : one CTA per angular row (m, j) of the log-polar grid: the sampled row (or, for
+//                Algorithm 2, g(S_m) on Omega_p sampled in place) and its real FFT along rho;
+//                writes the half spectrum.
 //   columns    : one CTA per group of rho frequencies: FFT along theta (zero-padded centre
 //                half), multiply by zeta_hat / B_hat (or zeta#_hat / B_hat), inverse FFT, keep
 //                the centre half plus a 2-row halo.
@@ -95,8 +97,8 @@ __device__ __forceinline__ float small_log1p(float u) {
 
 // ------------------------------------------------------------------------------------------
 // Pre-filters.  One CTA computes a kPfRows x kPfCols tile of coefficients from the tile plus a
-// kFirHalf halo, staged in shared memory; the FIR runs along rows and then along columns, each
-// thread producing kPfSeg consecutive outputs from a register window.  Tiles whose halo stays
+// kFirHalf halo, staged in shared memory; the filter runs along rows and then along columns,
+// each thread producing kPfSeg consecutive outputs from a register window.  Tiles whose halo stays
 // inside the array read it directly; border tiles map every index through the extension.
 
 constexpr int kPfRows = 32, kPfCols = 64, kPfSeg = 8;
@@ -166,8 +168,8 @@ struct SinoSource {
 // u[k] = w[k] + z u[k-1] from zero state at the window start, anticausal v[k] = u[k] + z v[k+1]
 // from zero state at the window end, c = -6 z v (the pair's impulse response is
 // -6 z / (1 - z^2) z^|n| = sqrt(3) z^|n|).  The zero states sit kFirHalf samples outside the
-// segment, so the response is cut at the same z^15 as the truncated FIR; 8 operations per
-// coefficient instead of 29.
+// segment, so the response is cut at z^15 ~ 2.7e-9, as a 29-tap truncated FIR would be, at 8
+// operations per coefficient instead of 29.
 __device__ __forceinline__ void segment_prefilter(float (&w)[kPfSeg + 2 * kFirHalf], float (&c)[kPfSeg]) {
   constexpr float z = -0.267949192431122706f;  // sqrt(3) - 2
   constexpr float g = -6.f * z;

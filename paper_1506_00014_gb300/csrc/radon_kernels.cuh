@@ -43,7 +43,6 @@ struct DevPlan {
   const int2* bp_e;
   const int4* bp_anc;  // 2 int4 per (m, tile)
   const float2* bp_m;
-  const float* fir;    // kFirHalf + 1
   const float* filt;   // FBP transfer functions / n_filt: 3 tables of n_filt/2 + 1 real bins
   // scratch
   float* coef_img;     // (N + 2 kPad)^2, zero border
