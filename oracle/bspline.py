@@ -14,6 +14,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
     extension of f that is odd about -1 and about n (period 2n + 2); the
     start values below are that extension's geometric sums.
   - "periodic": the sequence is periodic with period n.
+* ``spread2d`` is the transpose of ``interp2d`` (used by the exact transpose of
+  Algorithm 1).
 * ``interp_*`` evaluate Eq. wsumn: with k = floor(t) and alpha = t - k the
   value is  B(alpha+1) c_{k-1} + B(alpha) c_k + B(alpha-1) c_{k+1} +
   B(alpha-2) c_{k+2}  (the printed w_0..w_3 are listed in reverse order of
@@ -159,6 +161,28 @@ def interp2d(c, t0, t1, order=3, mode0="zero", mode1="zero"):
             i1, v1 = _index(k1 + d1, n1, mode1)
             val = c[i0, i1]
             out += np.where(v0 & v1, val, 0.0) * w0[..., d0] * w1[..., d1]
+    return out
+
+
+def spread2d(v, t0, t1, shape, order=3, mode0="zero", mode1="zero"):
+    """Transpose of ``interp2d`` with respect to ``c``: every value v (at fractional indices
+    (t0, t1), arrays of one shape) is added, times the tap weight, to each tap ``interp2d``
+    reads; taps that ``interp2d`` reads as zero are dropped, periodic taps wrap.  Returns an
+    array of ``shape``, so that sum(interp2d(c, t0, t1) * v) == sum(c * spread2d(v, t0, t1))."""
+    n0, n1 = shape
+    t0 = np.asarray(t0, dtype=np.float64)
+    t1 = np.asarray(t1, dtype=np.float64)
+    v = np.broadcast_to(np.asarray(v, dtype=np.float64), t0.shape)
+    k0, w0 = _taps(t0, order)
+    k1, w1 = _taps(t1, order)
+    ntap = w0.shape[-1]
+    out = np.zeros(shape)
+    for d0 in range(ntap):
+        i0, v0 = _index(k0 + d0, n0, mode0)
+        for d1 in range(ntap):
+            i1, v1 = _index(k1 + d1, n1, mode1)
+            ok = v0 & v1
+            np.add.at(out, (i0[ok], i1[ok]), (v * w0[..., d0] * w1[..., d1])[ok])
     return out
 
 

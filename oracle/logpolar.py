@@ -1,4 +1,5 @@
-"""Algorithm 1 (fast Radon transform) and Algorithm 2 (fast back-projection), FP64.
+"""Algorithm 1 (fast Radon transform), Algorithm 2 (fast back-projection) and the exact
+transpose of Algorithm 1, FP64.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
@@ -70,6 +71,26 @@ def logpolar_convolution(h_central: np.ndarray, K: np.ndarray, geo, dft: _Dft | 
     Fi = np.conj(dft.Frho)
     y = Yt.real @ Fi.real - Yt.imag @ Fi.imag  # real part of the inverse DFT along rho
     return y / (nt * nr)
+
+
+def logpolar_convolution_transpose(ybar: np.ndarray, K: np.ndarray, geo, dft: _Dft | None = None) -> np.ndarray:
+    """Transpose of ``logpolar_convolution`` (a real linear map h -> y).
+
+    The forward map is y = Re(A h) with the complex-linear
+    A h = conj(F_out) (K * (F_in h F_rho)) conj(F_rho) / (n_theta N_rho), where F_in are the
+    DFT columns of the central rows and F_out the inverse-DFT rows kept.  For real h and y,
+    sum(y * ybar) = sum(h * Re(A^T ybar)), and A^T applies the transposed factors in reverse
+    order (K acts elementwise and is its own transpose; F_rho is symmetric).
+    ``ybar``: (n_th_h + HALO_LO + HALO_HI) x N_rho; returns n_th_h x N_rho.
+    """
+    dft = dft or _Dft(geo)
+    nh, nt, nr = geo.n_th_h, geo.n_theta, geo.N_rho
+    rows_in = np.arange(nh // 2, nh // 2 + nh)
+    rows_out = np.arange(nh // 2 - HALO_LO, nh // 2 + nh + HALO_HI) % nt
+    Z = np.conj(dft.Fth[rows_out, :]).T @ np.asarray(ybar, dtype=np.float64) @ np.conj(dft.Frho).T
+    Z = Z * K
+    hb = dft.Fth[:, rows_in].T @ Z @ dft.Frho.T
+    return hb.real / (nt * nr)
 
 
 def image_coefficients(f: np.ndarray, geo) -> np.ndarray:
@@ -181,3 +202,60 @@ def backproject(g: np.ndarray, geo, K: np.ndarray | None = None, dft: _Dft | Non
         img[ii, jj_pix] += bspline.interp2d(y, cth, crho, order=geo.interp,
                                             mode0="zero", mode1="periodic")    # to X, summed over m
     return img
+
+
+def transpose(gbar: np.ndarray, geo, K: np.ndarray | None = None, dft: _Dft | None = None,
+              partitions=None, row_chunk: int = 32) -> np.ndarray:
+    """Exact transpose of the discrete map ``forward`` computes: sum(forward(f) * gbar) ==
+    sum(f * transpose(gbar)) for every f and gbar.  Returns float64 [N, N].
+
+    Algorithm 2 discretises the continuous adjoint R# instead, so R# is the transpose only up
+    to the discretisation error and a scale; this map is the one whose gradients are exact for
+    objectives built on ``forward``.  The steps of Algorithm 1 are transposed in reverse order:
+    the resampling to Sigma becomes spreading onto the log-polar coefficient grid, the
+    convolution becomes ``logpolar_convolution_transpose``, the resampling of T_m f on
+    Omega_lp becomes spreading onto the image coefficient grid, and Q (applied along both
+    axes) and the disc mask become Q^T and the mask.
+    """
+    N, M, r = geo.N, geo.M, geo.r
+    nh, nr = geo.n_th_h, geo.N_rho
+    K = kernels.multiplier(geo, "R") if K is None else K
+    dft = dft or _Dft(geo)
+    erho = np.exp(geo.rho(np.arange(nr)))
+    q = (np.arange(r) - (r - 1) / 2.0) * geo.dphi / r
+    live = live_bins(geo.n_det)
+    sk = (np.arange(geo.n_det) - geo.n_det / 2) * geo.ds
+    gbar = np.asarray(gbar, dtype=np.float64)
+    cbar = np.zeros((N, N))
+    for m in (range(M) if partitions is None else partitions):
+        ybar = np.zeros((nh + HALO_LO + HALO_HI, nr))
+        for a in range(geo.n_angles):                                    # transpose of S_m^{-1} Omega_p -> Sigma
+            am, num, flip = angle_partition(a, geo.n_angles, M)
+            if am != m:
+                continue
+            phi_a = num * math.pi / (M * geo.n_angles)
+            s = -sk if flip else sk
+            t = geo.a_R * s[live] + (1.0 - geo.a_R) * math.cos(phi_a)
+            crho = np.log(t) / geo.drho + nr - 1
+            cth = np.full(crho.shape, phi_a / geo.dphi + nh // 2 + HALO_LO)
+            ybar += bspline.spread2d(gbar[a, live] / geo.a_R, cth, crho, ybar.shape, order=geo.interp,
+                                     mode0="zero", mode1="periodic")
+        hbar = logpolar_convolution_transpose(ybar, K, geo, dft)          # transpose of the convolution
+        cm, sm = math.cos(m * geo.beta), math.sin(m * geo.beta)
+        for j0 in range(0, nh, row_chunk):                               # transpose of the resampling on Omega_lp
+            jj = np.arange(j0, min(nh, j0 + row_chunk))
+            phi = _sample_rows(geo, jj)[:, None, None] + q[None, :, None]
+            y1 = erho[None, None, :] * np.cos(phi)
+            y2 = erho[None, None, :] * np.sin(phi)
+            u1 = (y1 - (1.0 - geo.a_R)) / geo.a_R
+            u2 = y2 / geo.a_R
+            x1 = cm * u1 - sm * u2
+            x2 = sm * u1 + cm * u2
+            col = x1 * (N / 2) + N / 2
+            row = x2 * (N / 2) + N / 2
+            v = np.broadcast_to((hbar[jj, :] * erho[None, :] / r)[:, None, :], col.shape)
+            cbar += bspline.spread2d(v, row, col, (N, N), order=geo.interp)
+    if geo.interp == 3:
+        Qn = bspline.prefilter_zero(np.eye(N), axis=0)                   # Q x = Qn @ x; c = Qn f Qn^T
+        cbar = Qn.T @ cbar @ Qn
+    return np.where(disc_mask(N), cbar, 0.0)
