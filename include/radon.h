@@ -105,6 +105,18 @@ int radon_backproject(radon_plan plan, const float* d_sino, float* d_image, void
  * d_sino is not modified; the filtered sinogram lives in plan-owned memory. */
 int radon_fbp(radon_plan plan, const float* d_sino, float* d_image, int filter, void* stream);
 
+/* R^T: the exact transpose of the discrete map radon_forward computes (Algorithm 1 with every
+ * step transposed, in reverse order), d_sino [n_angles][n_det] -> d_image [N][N] (overwritten).
+ * sum(R f * g) = sum(f * R^T g) up to FP32 rounding, for every f and g, so R^T gives exact
+ * gradients of objectives built on radon_forward.  It is not R#: Algorithm 2 discretises the
+ * continuous adjoint, which R^T approaches only as dx^2 / (d_theta d_s) R# on smooth g (with a
+ * pixel-scale ripple from spreading over the log-polar samples).  Bins with |s| >= 1 are ignored;
+ * pixels outside the unit disc are zero.  The log-polar and image scatters accumulate with FP32
+ * atomics, so the low bits of the result may vary from run to run.  Uses the plan's scratch like
+ * the other transforms; radon_transpose_batch takes `batch` <= max_batch slices back to back. */
+int radon_transpose(radon_plan plan, const float* d_sino, float* d_image, void* stream);
+int radon_transpose_batch(radon_plan plan, const float* d_sinos, float* d_images, int batch, void* stream);
+
 /* Batches of same-size slices.  radon_plan_reserve_batch makes the plan able to process up to
  * max_batch slices in one call: it allocates scratch and texture storage for them, synchronising
  * the device (call it before any stream capture).  It returns RADON_NOT_SUPPORTED when the
@@ -149,13 +161,16 @@ int radon_kernel_quadrant(int N, int n_angles, int n_det, int n_partitions, int 
  * convolution, 3 forward inverse rho FFT, 4 sinogram gather, 5 sinogram pre-filter,
  * 6 back-projection row sampling + rho FFT, 7 back-projection theta convolution,
  * 8 back-projection inverse rho FFT, 9 image gather, 10 FBP filter along s, 11 forward row
- * sampling (log-polar resampling of the image). */
-#define RADON_NUM_STAGES 12
+ * sampling (log-polar resampling of the image); radon_transpose: 12 scatter of the sinogram
+ * onto the log-polar grid, 13 rho FFT, 14 transposed theta convolution, 15 inverse rho FFT,
+ * 16 scatter onto the image coefficients, 17 Q^T and the disc mask. */
+#define RADON_NUM_STAGES 18
 int radon_profile_enable(radon_plan plan, int enable);
 int radon_profile_read(radon_plan plan, double* ms, int* launches);
 
 /* Number of kernels one call launches with the plan's current settings: op 0 radon_forward,
- * 1 radon_backproject, 2 radon_fbp (a stage may launch more than one kernel).  Written to *out;
+ * 1 radon_backproject, 2 radon_fbp, 3 radon_transpose (a stage may launch more than one kernel;
+ * radon_transpose also clears its two scatter targets with cudaMemsetAsync).  Written to *out;
  * RADON_INVALID_ARG for another op. */
 int radon_plan_kernel_launches(radon_plan plan, int op, int* out);
 

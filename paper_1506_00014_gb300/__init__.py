@@ -30,4 +30,6 @@ from .binding import (  # noqa: F401
     radon_profile_enable,
     radon_profile_read,
     radon_status_string,
+    radon_transpose,
+    radon_transpose_batch,
 )

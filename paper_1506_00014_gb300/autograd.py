@@ -10,6 +10,10 @@ R# is the discretised adjoint of the continuous R (Algorithm 2), not the transpo
 Algorithm 1. The two agree to about 1e-5 relative on smooth inputs and differ more on rough
 ones, and that difference is what a finite-difference check of these gradients measures.
 
+``radon(image, plan, exact=True)`` takes the backward from radon_transpose instead: the exact
+transpose of the discrete forward map, so its gradients pass a finite-difference check to FP32
+rounding (no scale factor: it is the transpose for torch's plain sums).
+
 R is linear, so nothing is saved for backward.  Inputs of shape [N, N] / [n_angles, n_det] or
 batches [B, ...] of them.  A batch runs through the batched C ABI entry points in chunks of the
 plan's reserved capacity (radon_plan_reserve_batch; one slice per call when nothing is reserved),
@@ -63,6 +67,18 @@ class RadonFunction(torch.autograd.Function):
         return _apply(binding.radon_backproject, binding.radon_backproject_batch, plan, grad, plan.image_shape) * c_r, None
 
 
+class RadonExactFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, image, plan):
+        ctx.plan = plan
+        return _apply(binding.radon_forward, binding.radon_forward_batch, plan, image, plan.sino_shape)
+
+    @staticmethod
+    def backward(ctx, grad):
+        plan = ctx.plan
+        return _apply(binding.radon_transpose, binding.radon_transpose_batch, plan, grad, plan.image_shape), None
+
+
 class BackprojectFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, sino, plan):
@@ -76,9 +92,10 @@ class BackprojectFunction(torch.autograd.Function):
         return _apply(binding.radon_forward, binding.radon_forward_batch, plan, grad, plan.sino_shape) * c_b, None
 
 
-def radon(image: torch.Tensor, plan: binding.RadonPlan) -> torch.Tensor:
-    """R f for [N, N] or [B, N, N] float32 CUDA tensors (differentiable)."""
-    return RadonFunction.apply(image, plan)
+def radon(image: torch.Tensor, plan: binding.RadonPlan, exact: bool = False) -> torch.Tensor:
+    """R f for [N, N] or [B, N, N] float32 CUDA tensors (differentiable).  The backward is the
+    scaled R# (exact=False) or the exact transpose R^T (exact=True)."""
+    return (RadonExactFunction if exact else RadonFunction).apply(image, plan)
 
 
 def backproject(sino: torch.Tensor, plan: binding.RadonPlan) -> torch.Tensor:

@@ -40,15 +40,16 @@ EXPORTED = (
     "radon_geometry", "radon_kernel_quadrant", "radon_status_string", "radon_profile_enable",
     "radon_profile_read", "radon_forward_static_scratch", "radon_plan_reserve_batch",
     "radon_forward_batch", "radon_backproject_batch", "radon_plan_set_column_group",
-    "radon_plan_kernel_launches",
+    "radon_plan_kernel_launches", "radon_transpose", "radon_transpose_batch",
 )
 
-RADON_NUM_STAGES = 12
+RADON_NUM_STAGES = 18
 STAGE_NAMES = (
     "prefilter_image", "rows_fwd", "columns_fwd", "rows_inv_fwd", "gather_sino",
     "prefilter_sino", "rows_bp", "columns_bp", "rows_inv_bp", "gather_image", "sino_filter",
-    "sample_fwd",
+    "sample_fwd", "scatter_sino_t", "rows_t", "columns_t", "rows_inv_t", "scatter_image_t", "prefilter_t",
 )
+TRANSPOSE_STAGES = STAGE_NAMES[12:]
 
 _lib = None
 
@@ -78,7 +79,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.radon_plan_destroy.restype = None
     lib.radon_plan_get_info.argtypes = [_c_void_p, P(radon_plan_info)]
     for name in ("radon_forward", "radon_backproject", "radon_forward_host", "radon_backproject_host",
-                 "radon_forward_static_scratch"):
+                 "radon_forward_static_scratch", "radon_transpose"):
         getattr(lib, name).argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p]
     lib.radon_fbp.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_void_p]
     lib.radon_geometry.argtypes = [_c_int, _c_int, _c_int, _c_int, _c_int, P(radon_plan_info)]
@@ -86,7 +87,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.radon_plan_reserve_batch.argtypes = [_c_void_p, _c_int]
     lib.radon_plan_set_column_group.argtypes = [_c_void_p, _c_int]
     lib.radon_plan_kernel_launches.argtypes = [_c_void_p, _c_int, P(_c_int)]
-    for name in ("radon_forward_batch", "radon_backproject_batch"):
+    for name in ("radon_forward_batch", "radon_backproject_batch", "radon_transpose_batch"):
         getattr(lib, name).argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_void_p]
     lib.radon_profile_enable.argtypes = [_c_void_p, _c_int]
     lib.radon_profile_read.argtypes = [_c_void_p, P(ctypes.c_double), P(_c_int)]
@@ -210,6 +211,13 @@ def radon_backproject(plan: RadonPlan, sino, image, stream=None):
     return image
 
 
+def radon_transpose(plan: RadonPlan, sino, image, stream=None):
+    """R^T, the exact transpose of radon_forward's discrete map (not R#)."""
+    _check(load().radon_transpose(plan.handle, _dev(sino, plan.sino_shape, "sino"),
+                                  _dev(image, plan.image_shape, "image"), _stream(stream, sino)), "radon_transpose")
+    return image
+
+
 def radon_fbp(plan: RadonPlan, sino, image, filter: int = RADON_FILTER_RAMP, stream=None):
     _check(load().radon_fbp(plan.handle, _dev(sino, plan.sino_shape, "sino"), _dev(image, plan.image_shape, "image"),
                             int(filter), _stream(stream, sino)), "radon_fbp")
@@ -257,9 +265,9 @@ def radon_profile_read(plan: RadonPlan):
 
 
 def radon_plan_kernel_launches(plan: RadonPlan, op: str) -> int:
-    """Kernels one call of op ("forward", "backproject" or "fbp") launches."""
+    """Kernels one call of op ("forward", "backproject", "fbp" or "transpose") launches."""
     n = _c_int()
-    code = {"forward": 0, "backproject": 1, "fbp": 2}[op]
+    code = {"forward": 0, "backproject": 1, "fbp": 2, "transpose": 3}[op]
     _check(load().radon_plan_kernel_launches(plan.handle, code, ctypes.byref(n)), "radon_plan_kernel_launches")
     return n.value
 
@@ -290,4 +298,13 @@ def radon_backproject_batch(plan: RadonPlan, sinos, images, stream=None):
     _check(load().radon_backproject_batch(plan.handle, _dev(sinos, (b,) + plan.sino_shape, "sinos"),
                                           _dev(images, (b,) + plan.image_shape, "images"), b, _stream(stream, sinos)),
            "radon_backproject_batch")
+    return images
+
+
+def radon_transpose_batch(plan: RadonPlan, sinos, images, stream=None):
+    """sinos [B, n_angles, n_det] -> images [B, N, N]: R^T of each slice."""
+    b = sinos.shape[0]
+    _check(load().radon_transpose_batch(plan.handle, _dev(sinos, (b,) + plan.sino_shape, "sinos"),
+                                        _dev(images, (b,) + plan.image_shape, "images"), b, _stream(stream, sinos)),
+           "radon_transpose_batch")
     return images

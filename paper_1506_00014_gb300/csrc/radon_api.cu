@@ -444,6 +444,19 @@ int radon_backproject_host(radon_plan plan, const float* h_sino, float* h_image,
   return status_of(e);
 }
 
+int radon_transpose(radon_plan plan, const float* d_sino, float* d_image, void* stream) {
+  if (!plan || !d_sino || !d_image) return RADON_INVALID_ARG;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  return status_of(radon::launch_transpose(plan->dp, d_sino, d_image, static_cast<cudaStream_t>(stream), hook_of(plan)));
+}
+
+int radon_transpose_batch(radon_plan plan, const float* d_sinos, float* d_images, int batch, void* stream) {
+  if (!plan || !d_sinos || !d_images || batch < 1 || batch > plan->dp.batch_cap) return RADON_INVALID_ARG;
+  if (!on_plan_device(plan)) return RADON_INVALID_ARG;
+  return status_of(
+      radon::launch_transpose(plan->dp, d_sinos, d_images, static_cast<cudaStream_t>(stream), hook_of(plan), batch));
+}
+
 int radon_plan_reserve_batch(radon_plan plan, int max_batch) {
   if (!plan || max_batch < 1) return RADON_INVALID_ARG;
   if (!on_plan_device(plan)) return RADON_INVALID_ARG;

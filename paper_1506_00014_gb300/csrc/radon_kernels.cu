@@ -104,10 +104,16 @@ __device__ __forceinline__ float small_log1p(float u) {
 constexpr int kPfRows = 32, kPfCols = 64, kPfSeg = 8;
 constexpr int kPfInR = kPfRows + 2 * kFirHalf, kPfInC = kPfCols + 2 * kFirHalf;
 
+// Sources of the pre-filter.  Each gives the tile input (direct / extended reads), says when a
+// window is all zero (dead), where its output columns start (kOutPad) and which outputs are kept
+// (keep; the rest are written as zero).
+
 // Masked image; extension odd about -1 and N in both axes (zero boundary, Eq. Qfrecursive).
 struct ImageSource {
+  static constexpr int kOutPad = kPad;  // output: padded coefficient image
   const float* __restrict__ f;
   int N;
+  __device__ __forceinline__ bool keep(int, int) const { return true; }
   __device__ __forceinline__ void slice(int b) { f += static_cast<size_t>(b) * N * N; }
   __device__ __forceinline__ bool interior(int r0, int r1, int c0, int c1) const {
     return r0 >= 0 && r1 <= N && c0 >= 0 && c1 <= N;
@@ -137,8 +143,10 @@ struct ImageSource {
 // Sinogram rows a (theta periodic over 2 n_angles, rows >= n_angles flipped k -> n_det - k) and
 // columns k in [0, n_det] (the extra k = n_det is zero); zero boundary in k; dead bins zero.
 struct SinoSource {
+  static constexpr int kOutPad = kPad;  // output: padded sinogram coefficients
   const float* __restrict__ g;
   int na, nd, live_lo, live_hi;
+  __device__ __forceinline__ bool keep(int, int) const { return true; }
   __device__ __forceinline__ void slice(int b) { g += static_cast<size_t>(b) * na * nd; }
   __device__ __forceinline__ bool interior(int r0, int r1, int c0, int c1) const {
     return r0 >= 0 && r1 <= na && c0 >= 0 && c1 <= nd + 1;
@@ -161,6 +169,34 @@ struct SinoSource {
     const int k = flip ? nd - q : q;
     return sc * direct(flip ? a2 - na : a2, k);
   }
+};
+
+// Q^T for the exact transpose: the padded coefficient grid (N x N inside a kPad border), with
+// the same odd extension as ImageSource.  The zero-boundary Q is a symmetric matrix (the
+// filter's taps are even and the odd reflections about -1 and N enter as h(i + j + 2) and
+// h(2N - i - j)), so Q^T is Q; the output is the unpadded image, zero outside the disc (the
+// transpose of the input mask).
+struct CoefSource {
+  static constexpr int kOutPad = 0;
+  const float* __restrict__ c;
+  int N, pitch;
+  size_t bstride;
+  __device__ __forceinline__ void slice(int b) { c += b * bstride; }
+  __device__ __forceinline__ bool interior(int r0, int r1, int c0, int c1) const {
+    return r0 >= 0 && r1 <= N && c0 >= 0 && c1 <= N;
+  }
+  __device__ __forceinline__ float direct(int r, int col) const {
+    return __ldg(c + static_cast<size_t>(r + kPad) * pitch + col + kPad);
+  }
+  __device__ __forceinline__ bool dead(int, int, int, int) const { return false; }
+  __device__ __forceinline__ float extended(int r, int col) const {
+    float sr, sc;
+    const int rr = odd_ext(r, N, &sr);
+    const int cc = odd_ext(col, N, &sc);
+    const float sg = sr * sc;
+    return sg != 0.f ? sg * direct(rr, cc) : 0.f;
+  }
+  __device__ __forceinline__ bool keep(int r, int col) const { return in_disc(r, col, N); }
 };
 
 // Pre-filter of one segment: the kPfSeg coefficients at the centre of a window of kPfSeg +
@@ -217,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
       for (int idx = tid; idx < kPfRows * kPfCols; idx += kThreads) {
         const int y = idx / kPfCols, lx = idx - y * kPfCols;
         const int gr = orow + y, gc = ccol + lx;
-        if (gr < n_rows && gc < n_cols) out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = 0.f;
+        if (gr < n_rows && gc < n_cols) out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + Src::kOutPad] = 0.f;
       }
     }
     return;
@@ -250,8 +286,8 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
     for (int idx = tid; idx < kPfRows * kPfCols; idx += kThreads) {
       const int ly = idx / kPfCols, lx = idx - ly * kPfCols;
       if (orow + ly < n_rows && ocol + lx < n_cols) {
-        const float v = s_in[ly + kFirHalf][lx + kFirHalf];
-        out[static_cast<size_t>(orow + ly + out_r0) * out_pitch + ocol + lx + kPad] = v;
+        const float v = src.keep(orow + ly, ocol + lx) ? s_in[ly + kFirHalf][lx + kFirHalf] : 0.f;
+        out[static_cast<size_t>(orow + ly + out_r0) * out_pitch + ocol + lx + Src::kOutPad] = v;
       }
     }
     return;
@@ -284,7 +320,7 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
       if constexpr (QUAD) {
         s_in[sy + t][lx] = (gc >= 0 && gc < n_cols) ? acc : 0.f;  // s_in is free after the row pass
       } else if (gr < n_rows && gc < n_cols) {
-        out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + kPad] = acc;
+        out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + Src::kOutPad] = src.keep(gr, gc) ? acc : 0.f;
       }
     }
   }
@@ -918,6 +954,256 @@ __global__ void __launch_bounds__(kPTile * kPTile, 6) k_gather_image(DevPlan p, 
   img[static_cast<size_t>(i) * N + j] = acc * lp_gain_inv(p);
 }
 
+// ------------------------------------------------------------------------------------------
+// Exact transpose R^T of the discrete forward map (the launches above, in reverse order, each
+// replaced by its transpose).  Gathers become scatters (atomic adds at the same taps with the
+// same weights and coordinates), the convolution with K becomes the convolution with conj(K)
+// from the kept rows back to the centre half, and the pre-filter becomes Q^T = Q followed by the
+// disc mask.  The log-polar scatter target is yspec read as real rows of 2 x_pitch floats.
+
+// Padded index inside the image (not in the kPad zero border) of a P = N + 2 kPad wide array.
+__device__ __forceinline__ bool interior_tap(int c, int P) { return c >= kPad && c < P - kPad; }
+
+__device__ __forceinline__ float* lp_real_rows(const DevPlan& p, int b) {
+  return reinterpret_cast<float*>(p.yspec + b * p.bs_ys);
+}
+
+// Transpose of k_gather_sino: g(theta_a, s_k) / a_R is added to the 16 (cubic) or 4 (linear)
+// log-polar coefficients the gather reads.  Padded column c holds rho index (c - kPad) mod
+// N_rho (the wrap columns written by k_rows_inv), so the scatter wraps the same way.
+__global__ void __launch_bounds__(128) k_scatter_sino(DevPlan p, const float* __restrict__ sino) {
+  const int a = blockIdx.y, b = blockIdx.z;
+  const int k = blockIdx.x * 128 + threadIdx.x;
+  const int nd = p.n_det;
+  if (k >= nd || k < p.live_lo || k > p.live_hi) return;
+  const float v = __ldg(sino + (static_cast<size_t>(b) * p.n_angles + a) * nd + k) * (p.inv_aR * lp_gain_inv(p));
+  if (v == 0.f) return;
+  const int4 ang = p.fwd_ang[a];
+  const int4 anc = p.fwd_anc[static_cast<size_t>(a) * p.n_ktiles + k / kKTile];
+  const int n = k - (k / kKTile) * kKTile;
+  const float cr = fmaf(log1pf(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
+  const float fr = floorf(cr);
+  const int It = ang.z, Ir = anc.x + static_cast<int>(fr);
+  const float at = __int_as_float(ang.w), ar = cr - fr;
+  const int nrow = p.nh + kHaloLo + kHaloHi, nr = p.N_rho, yp = 2 * p.x_pitch, wrap_end = nr + 2 * kPad;
+  float* y = lp_real_rows(p, b) + static_cast<size_t>(ang.x) * nrow * yp;
+  if (p.interp == 3) {
+    float2 w[4];  // .x: theta weights, .y: rho weights (times 6 each)
+    bspline_w6_pair(make_float2(at, ar), w);
+    const int r0 = clampi(It - 1, 0, nrow - 4), c0 = clampi(Ir - 1, 0, p.y_pitch - 4);
+#pragma unroll
+    for (int dt = 0; dt < 4; ++dt) {
+      float* row = y + static_cast<size_t>(r0 + dt) * yp;
+      const float vt = v * w[dt].x;
+#pragma unroll
+      for (int dc = 0; dc < 4; ++dc) {
+        const int pc = c0 + dc;
+        if (pc >= wrap_end) continue;
+        int col = pc - kPad;
+        col = col < 0 ? col + nr : (col >= nr ? col - nr : col);
+        atomicAdd(row + col, vt * w[dc].y);
+      }
+    }
+  } else {
+    const int r0 = clampi(It, 0, nrow - 2), c0 = clampi(Ir, 0, p.y_pitch - 2);
+    const float wt[2] = {1.f - at, at}, wr[2] = {1.f - ar, ar};
+#pragma unroll
+    for (int dt = 0; dt < 2; ++dt) {
+      float* row = y + static_cast<size_t>(r0 + dt) * yp;
+#pragma unroll
+      for (int dc = 0; dc < 2; ++dc) {
+        const int pc = c0 + dc;
+        if (pc >= wrap_end) continue;
+        int col = pc - kPad;
+        col = col < 0 ? col + nr : (col >= nr ? col - nr : col);
+        atomicAdd(row + col, v * wt[dt] * wr[dc]);
+      }
+    }
+  }
+}
+
+// Real FFT along rho of one kept row, in place: the row's N_rho reals become its half spectrum
+// (N_rho/2 + 1 bins); same transform and post-processing as k_rows_fwd.
+__global__ void __launch_bounds__(kThreads) k_rows_r2c_t(DevPlan p) {
+  extern __shared__ __align__(16) float2 smem[];
+  const int nc = p.nc;
+  float2* bufA = smem;
+  float2* bufB = smem + nc;
+  float2* tws = smem + 2 * nc;
+  if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
+  const float2* tw = p.rows_tw_smem ? tws : p.tw_rho;
+  const int row = blockIdx.x, m = blockIdx.y, b = blockIdx.z;
+  const int nrow = p.nh + kHaloLo + kHaloHi;
+  float2* X = p.yspec + b * p.bs_ys + (static_cast<size_t>(m) * nrow + row) * p.x_pitch;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) bufA[k] = X[k];
+  __syncthreads();  // the whole row is in shared memory before the first write below
+  const float2* Z = fft_block<false>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
+  for (int k = threadIdx.x; k <= nc; k += blockDim.x) {
+    const float2 zk = Z[k == nc ? 0 : k];
+    const float2 zc = cconj(Z[k == 0 ? 0 : nc - k]);
+    const float2 ev = cscale(cadd(zk, zc), 0.5f);
+    const float2 dv = cscale(csub(zk, zc), 0.5f);
+    const float2 od = make_float2(dv.y, -dv.x);
+    X[k] = cadd(ev, cmul(p.tw_r2c[k], od));
+  }
+}
+
+// Transposed theta convolution of G rho frequencies: the kept rows (centre half plus halo) are
+// placed at their lattice rows, transformed, multiplied by conj(K), transformed back, and the
+// centre half is written to xspec.
+__global__ void __launch_bounds__(kThreads) k_columns_t(DevPlan p, const float2* __restrict__ kern, int G) {
+  extern __shared__ __align__(16) float2 smem[];
+  const int nt = p.n_theta, nh = p.nh, nc = p.nc;
+  const int nrow = nh + kHaloLo + kHaloHi;
+  float2* A = smem;
+  float2* B = smem + G * nt;
+  float2* tw = smem + 2 * G * nt;
+  stage_table(tw, p.tw_th, nt, threadIdx.x, blockDim.x);
+  const int m = blockIdx.y, kr0 = blockIdx.x * G, b = blockIdx.z;
+  const float2* yin = p.yspec + b * p.bs_ys + static_cast<size_t>(m) * nrow * p.x_pitch;
+  for (int idx = threadIdx.x; idx < G * nt; idx += blockDim.x) {
+    const int g = idx % G, j = idx / G;
+    // kept rows jr = j - nh/2 + kHaloLo (mod nt) come from lattice row j; with nt < nrow (tiny
+    // grids) two kept rows share a lattice row and the transpose sums them
+    float2 v = make_float2(0.f, 0.f);
+    if (kr0 + g <= nc)
+      for (int jr = (j - nh / 2 + kHaloLo + nt) % nt; jr < nrow; jr += nt)
+        v = cadd(v, yin[static_cast<size_t>(jr) * p.x_pitch + kr0 + g]);
+    A[g * nt + j] = v;
+  }
+  __syncthreads();
+  float2* S = fft_block<false>(A, B, G, nt, p.rad_th, tw, threadIdx.x, blockDim.x);
+  float2* T = (S == A) ? B : A;
+  const int nkt = nt / 2 + 1;
+  for (int idx = threadIdx.x; idx < G * nt; idx += blockDim.x) {
+    const int g = idx / nt, pp = idx - g * nt;
+    const int kr = kr0 + g;
+    if (kr <= nc) {
+      const int kt = pp <= nt - pp ? pp : nt - pp;
+      S[idx] = cmul(S[idx], cconj(kern[static_cast<size_t>(kr) * nkt + kt]));
+    }
+  }
+  __syncthreads();
+  const float2* Y = fft_block<true>(S, T, G, nt, p.rad_th, tw, threadIdx.x, blockDim.x);
+  float2* xout = p.xspec + b * p.bs_x + static_cast<size_t>(m) * nh * p.x_pitch;
+  for (int idx = threadIdx.x; idx < G * nh; idx += blockDim.x) {
+    const int g = idx % G, jj = idx / G;
+    if (kr0 + g <= nc) xout[static_cast<size_t>(jj) * p.x_pitch + kr0 + g] = Y[g * nt + jj + nh / 2];
+  }
+}
+
+// Inverse real FFT along rho of one centre-half row of xspec (same pre-processing as
+// k_rows_inv); the N_rho reals go to yspec row m nh + jj, where k_scatter_fwd reads them.
+__global__ void __launch_bounds__(kThreads) k_rows_c2r_t(DevPlan p) {
+  extern __shared__ __align__(16) float2 smem[];
+  const int nc = p.nc, nr = p.N_rho;
+  float2* bufA = smem;
+  float2* bufB = smem + nc;
+  float2* tws = smem + 2 * nc;
+  if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
+  const float2* tw = p.rows_tw_smem ? tws : p.tw_rho;
+  const int jj = blockIdx.x, m = blockIdx.y, b = blockIdx.z;
+  const float2* X = p.xspec + b * p.bs_x + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const float2 xk = X[k];
+    const float2 xc = cconj(X[nc - k]);
+    const float2 sm = cadd(xk, xc);
+    const float2 df = cmulc(csub(xk, xc), p.tw_r2c[k]);
+    bufA[k] = make_float2(sm.x - df.y, sm.y + df.x);
+  }
+  __syncthreads();
+  const float2* Z = fft_block<true>(bufA, bufB, 1, nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
+  const float* h = reinterpret_cast<const float*>(Z);
+  float* out = reinterpret_cast<float*>(p.yspec + b * p.bs_ys + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch);
+  for (int c = threadIdx.x; c < nr; c += blockDim.x) out[c] = h[c];
+}
+
+// Transpose of k_sample_fwd: the same warps, anchors, ranges and FP32 coordinates; each fine
+// sample adds h(phi_j, rho_i) e^rho_i / r times its tap weights to the padded coefficient image
+// coef_img (zeroed beforehand).  Tap blocks are bounds-checked like sample_image, and taps in the
+// zero border are dropped (the forward reads them as constants), so the border stays zero.
+__global__ void __launch_bounds__(kSampleWarps * 32) k_scatter_fwd(DevPlan p) {
+  extern __shared__ __align__(16) float4 sanc[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = p.r, ne = p.n_eanc;
+  const int tile0 = 2 * blockIdx.x, m = blockIdx.z % p.M, b = blockIdx.z / p.M;
+  const int jj = blockIdx.y * kSampleWarps + warp;
+  if (jj >= p.nh) return;
+  float4* anc = sanc + warp * 2 * r;
+  float2* dir = reinterpret_cast<float2*>(sanc + kSampleWarps * 2 * r) + warp * r;
+  int2* rng = reinterpret_cast<int2*>(reinterpret_cast<float2*>(sanc + kSampleWarps * 2 * r) + kSampleWarps * r) + warp * r;
+  const float4 um = p.fwd_m[m];
+  const size_t row0 = (static_cast<size_t>(m) * p.nh + jj) * r;
+  const float4* rowc = p.fwd_row + row0;
+  const float2 ea0 = p.fwd_eanc[tile0];
+  const float2 ea1 = p.fwd_eanc[tile0 + 1 < ne ? tile0 + 1 : tile0];
+  for (int q = lane; q < r; q += 32) {
+    const float4 cs = rowc[q];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float2 ea = u ? ea1 : ea0;
+      float ch, cl, rh, rl;
+      df_mul_add(ea.x, ea.y, cs.x, cs.y, um.x, um.y, &ch, &cl);
+      df_mul_add(ea.x, ea.y, cs.z, cs.w, um.z, um.w, &rh, &rl);
+      const float Ic = floorf(ch), Ir = floorf(rh);
+      anc[u * r + q] = make_float4(Ic, (ch - Ic) + cl, Ir, (rh - Ir) + rl);
+    }
+    dir[q] = make_float2(cs.x, cs.z);
+    rng[q] = p.fwd_rng[row0 + q];
+  }
+  __syncwarp();
+  const int base = tile0 * kETile;
+  const int i0 = base + lane, i1 = i0 + kETile;
+  const float* hrow = reinterpret_cast<const float*>(p.yspec + b * p.bs_ys + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch);
+  const float scale = p.interp == 3 ? 1.f / 36.f : 1.f;
+  const float2 e0 = i0 < p.N_rho ? p.fwd_e[i0] : make_float2(0.f, 0.f);
+  const float2 e1 = i1 < p.N_rho ? p.fwd_e[i1] : make_float2(0.f, 0.f);
+  const float v0 = i0 < p.N_rho ? hrow[i0] * e0.x * scale : 0.f;
+  const float v1 = i1 < p.N_rho ? hrow[i1] * e1.x * scale : 0.f;
+  const int P = p.img_pitch;
+  float* __restrict__ img = p.coef_img + b * p.bs_img;
+  for (int q = 0; q < r; ++q) {
+    const int2 rg = rng[q];
+    if (rg.y < base || rg.x > base + 2 * kETile - 1) continue;
+    const float2 d = dir[q];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = u ? i1 : i0;
+      const float v = u ? v1 : v0;
+      if (i < rg.x || i > rg.y || v == 0.f) continue;
+      const float4 a = anc[u * r + q];
+      const float ey = u ? e1.y : e0.y;
+      const float Fc = fmaf(ey, d.x, a.y), Fr = fmaf(ey, d.y, a.w);
+      const float fc = floorf(Fc), fr = floorf(Fr);
+      const int ic = static_cast<int>(a.x + fc), ir = static_cast<int>(a.z + fr);
+      if (p.interp == 3) {
+        if (ic < 1 || ic > P - 3 || ir < 1 || ir > P - 3) continue;
+        float2 w[4];  // .x: column weights, .y: row weights (times 6 each)
+        bspline_w6_pair(make_float2(Fc - fc, Fr - fr), w);
+        float* t = img + static_cast<size_t>(ir - 1) * P + (ic - 1);
+#pragma unroll
+        for (int dr = 0; dr < 4; ++dr) {
+          if (!interior_tap(ir - 1 + dr, P)) continue;
+          const float vr = v * w[dr].y;
+#pragma unroll
+          for (int dc = 0; dc < 4; ++dc)
+            if (interior_tap(ic - 1 + dc, P)) atomicAdd(t + dr * P + dc, vr * w[dc].x);
+        }
+      } else {
+        if (ic < 0 || ic > P - 2 || ir < 0 || ir > P - 2) continue;
+        const float ac = Fc - fc, ar = Fr - fr;
+        const float wr[2] = {1.f - ar, ar}, wc[2] = {1.f - ac, ac};
+        float* t = img + static_cast<size_t>(ir) * P + ic;
+#pragma unroll
+        for (int dr = 0; dr < 2; ++dr)
+#pragma unroll
+          for (int dc = 0; dc < 2; ++dc)
+            if (interior_tap(ir + dr, P) && interior_tap(ic + dc, P)) atomicAdd(t + dr * P + dc, v * wr[dr] * wc[dc]);
+      }
+    }
+  }
+}
+
 // FBP: filter one sinogram row along s (Eq. FBP, Eq. ramp / SLfilt / cosfilt).  The row (bins
 // with |s| >= 1 zeroed) is zero-padded to n_filt, transformed with the real FFT, multiplied by
 // the real transfer function H (divided by n_filt) and transformed back; the first n_det values
@@ -980,6 +1266,7 @@ size_t sample_fwd_smem(const DevPlan& p) {
   return static_cast<size_t>(kSampleWarps) * p.r * (2 * sizeof(float4) + sizeof(float2) + sizeof(int2));
 }
 size_t cols_smem(const DevPlan& p) { return (2 * static_cast<size_t>(p.col_group) + 1) * p.n_theta * sizeof(float2); }
+size_t cols_t_smem(const DevPlan& p, int G) { return (2 * static_cast<size_t>(G) + 1) * p.n_theta * sizeof(float2); }
 
 template <bool BACK>
 void launch_rows_forward(const DevPlan& p, cudaStream_t st, int batch) {
@@ -1053,6 +1340,14 @@ cudaError_t configure_kernels(DevPlan& p) {
   RADON_ROW_SEQUENCES(RADON_CONFIGURE_ROWS)
 #undef RADON_CONFIGURE_ROWS
   if ((e = cudaFuncSetAttribute(k_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess) return e;
+  // exact transpose: generic kernels; the theta pass takes the widest group that fits
+  if ((e = cudaFuncSetAttribute(k_rows_r2c_t, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_rows_c2r_t, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_scatter_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_columns_t, cudaFuncAttributeMaxDynamicSharedMemorySize, cs)) != cudaSuccess) return e;
+  p.col_group_t = 0;
+  for (int G = 4; G >= 1 && !p.col_group_t; G /= 2)
+    if (cols_t_smem(p, G) <= static_cast<size_t>(optin)) p.col_group_t = G;
   p.col_blocks = 0;
   if (p.col_fixed >= 0) {
     int n_sm = 0;
@@ -1114,7 +1409,36 @@ cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image
 int kernel_launches(const DevPlan& p, int op) {
   const int fwd = 6;  // prefilter, sample, rows, columns, rows_inv, gather
   const int bp = 5;   // prefilter, rows, columns, rows_inv, gather
-  return op == 0 ? fwd : op == 1 ? bp : op == 2 ? bp + 1 : -1;
+  const int tr = 6;   // scatter to log-polar, rows, columns, rows_inv, scatter to the image, Q^T
+  return op == 0 ? fwd : op == 1 ? bp : op == 2 ? bp + 1 : op == 3 ? tr : -1;
+}
+
+cudaError_t launch_transpose(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook,
+                             int batch) {
+  if (batch < 1 || batch > p.batch_cap || p.col_group_t < 1) return cudaErrorInvalidValue;
+  hook(-1, st);
+  // scatter targets: the log-polar rows (yspec) and the padded coefficient image
+  cudaError_t e = cudaMemsetAsync(p.yspec, 0, sizeof(float2) * p.bs_ys * batch, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p.coef_img, 0, sizeof(float) * p.bs_img * batch, st);
+  if (e != cudaSuccess) return e;
+  const int nrow = p.nh + kHaloLo + kHaloHi;
+  k_scatter_sino<<<dim3((p.n_det + 127) / 128, p.n_angles, batch), 128, 0, st>>>(p, sino);
+  hook(12, st);
+  k_rows_r2c_t<<<dim3(nrow, p.M, batch), kThreads, rows_smem(p), st>>>(p);
+  hook(13, st);
+  const int G = p.col_group_t;
+  k_columns_t<<<dim3((p.nc + 1 + G - 1) / G, p.M, batch), kThreads, cols_t_smem(p, G), st>>>(p, p.k_fwd, G);
+  hook(14, st);
+  k_rows_c2r_t<<<dim3(p.nh, p.M, batch), kThreads, rows_smem(p), st>>>(p);
+  hook(15, st);
+  const dim3 sgrid((p.n_eanc + 1) / 2, (p.nh + kSampleWarps - 1) / kSampleWarps, p.M * batch);
+  k_scatter_fwd<<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
+  hook(16, st);
+  const CoefSource csrc{p.coef_img, p.N, p.img_pitch, p.bs_img};
+  k_prefilter<CoefSource, false><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows, batch),
+                                   kThreads, 0, st>>>(p, csrc, p.N, p.N, image, p.N, 0, static_cast<size_t>(p.N) * p.N);
+  hook(17, st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fbp(const DevPlan& p, const float* sino, float* image, int filter, cudaStream_t st, StageHook hook) {

@@ -21,6 +21,7 @@ struct DevPlan {
   int col_group;   // generic column kernel: rho frequencies per CTA (4, 2 or 1); 0: specialised kernel
   int col_fixed;   // kColumnRadices index of the specialised column kernel, -1 if none
   int col_blocks;  // persistent grid of the specialised column kernel (resident CTAs on the device)
+  int col_group_t; // rho frequencies per CTA of the transposed theta pass (0: does not fit)
   int live_lo, live_hi;  // detector bins with |s| < 1 are exactly [live_lo, live_hi]
   float inv_drho, inv_dphi, inv_aR, d_s;
   RadixList rad_rho, rad_th;
@@ -85,8 +86,12 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
 cudaError_t launch_backproject(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook,
                                int batch = 1);
 cudaError_t launch_fbp(const DevPlan& p, const float* sino, float* image, int filter, cudaStream_t st, StageHook hook);
+// Exact transpose of launch_forward's map (stages 12-17).
+cudaError_t launch_transpose(const DevPlan& p, const float* sino, float* image, cudaStream_t st, StageHook hook,
+                             int batch = 1);
 
-// Kernels launched by launch_forward (op 0), launch_backproject (1) and launch_fbp (2).
+// Kernels launched by launch_forward (op 0), launch_backproject (1), launch_fbp (2) and
+// launch_transpose (3).
 int kernel_launches(const DevPlan& p, int op);
 
 // Dynamic shared memory limits are raised once per device.

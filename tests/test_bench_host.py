@@ -21,7 +21,8 @@ def _info():
 
 def test_byte_model_covers_the_transform_stages():
     model = bench.stage_bytes(_info())
-    stages = set(binding.STAGE_NAMES) - {"sino_filter"}  # the FBP filter is not part of the pair
+    # the FBP filter and the exact transpose are not part of the pair
+    stages = set(binding.STAGE_NAMES) - {"sino_filter"} - set(binding.TRANSPOSE_STAGES)
     assert set(model) == stages
     assert all(v > 0 for v in model.values())
 
