@@ -266,6 +266,35 @@ def bench_fbp_large(rl, torch, flush) -> dict:
             "accuracy": "closed form (FBP of analytic Gaussians) checked in tests/test_gpu_parity.py"}
 
 
+def bench_exact_transpose(rl, torch, flush) -> dict:
+    """R^T (radon_transpose, the exact transpose of the discrete R) on the headline workload
+    (N = 2048, 2048 angles x 3072 bins, cubic, M = 3) beside R and R# of the same plan, each
+    timed alone; plus R^T's per-stage split from the profiling events (a separate pass)."""
+    plan = rl.radon_plan_create(N, N_ANGLES, N_DET, INTERP, M)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    g = torch.randn((N_ANGLES, N_DET), device="cuda", generator=gen)
+    f = torch.rand((N, N), device="cuda", generator=gen)
+    img = torch.empty((N, N), device="cuda")
+    sino = torch.empty((N_ANGLES, N_DET), device="cuda")
+    calls = {"R": lambda: rl.radon_forward(plan, f, sino), "R#": lambda: rl.radon_backproject(plan, g, img),
+             "R^T": lambda: rl.radon_transpose(plan, g, img)}
+    out = {}
+    for name, fn in calls.items():
+        for _ in range(3):
+            fn()
+        out["ms_" + name] = _event_ms(torch, fn, 20, flush)
+    rl.radon_profile_enable(plan, True)
+    rl.radon_profile_read(plan)
+    for _ in range(5):
+        calls["R^T"]()
+    stages = rl.radon_profile_read(plan)
+    rl.radon_profile_enable(plan, False)
+    out["stage_ms_R^T"] = {k: round(ms / n, 4) for k, (ms, n) in stages.items() if n}
+    out["accuracy"] = ("parity with the oracle's transpose of Algorithm 1 and the dot-product identity, "
+                       "tests/test_gpu_transpose.py")
+    return out
+
+
 def bench_em_volume(rl, torch, n: int = 256, iters: int = 100) -> dict:
     """100 EM iterations (Section 8) on an n x n x n volume: n slices, 1.5 n angles, n bins,
     M = 3 (the paper's EM timing setup), data = analytic line integrals of non-negative random
@@ -542,6 +571,7 @@ def run_ours(args):
         extras["batched"] = bench_batched(rl, torch, flush)
         extras["least_squares"] = bench_least_squares(rl, torch)
         extras["fbp_8192"] = bench_fbp_large(rl, torch, flush)
+        extras["exact_transpose"] = bench_exact_transpose(rl, torch, flush)
         extras["paper_table1_backprojection"] = bench_paper_table1(rl, torch, flush)
         extras["em_volume_256"] = bench_em_volume(rl, torch, 256)
         extras["em_volume_512"] = bench_em_volume(rl, torch, 512)
