@@ -497,7 +497,7 @@ def run_ours(args):
     dom_ms = stage[dom][0] / max(1, stage[dom][1])
     peak, peak_kind = _peaks()
     achieved = nbytes[dom] / (dom_ms / 1e3) / 1e9
-    stage_ms = {k: round(v[0] / max(1, v[1]), 4) for k, v in stage.items()}
+    stage_ms = {k: round(v[0] / v[1], 4) for k, v in stage.items() if v[1]}  # stages the pair launched
     traffic = _dram_traffic().get(dom)
     summary = _ncu_summary().get(dom)
 
