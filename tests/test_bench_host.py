@@ -36,3 +36,20 @@ def test_dram_traffic_summary_names_known_stages():
 
 def test_samples_per_step_counts_both_outputs():
     assert bench._samples_per_step() == bench.N_ANGLES * bench.N_DET + bench.N * bench.N
+
+
+def test_direct_oracle_sampling_runs_and_reports_each_result():
+    import numpy as np
+
+    from oracle import geometry, logpolar
+    from workloads import ellipse_image, random_ellipses, random_sinogram
+
+    geo = geometry.make_geometry(64, 48, 96, 3, 3)
+    f = ellipse_image(64, random_ellipses(10, 2))
+    g = random_sinogram(48, 96, 3)
+    rf, bg = logpolar.forward(f, geo), logpolar.backproject(g, geo)
+    out = bench.err_vs_direct(geo, f, g, {"a": (rf, bg), "b": (rf.astype(np.float32), bg.astype(np.float32))},
+                              n_ang=8, n_bins=16, n_pix=64)
+    assert out["a"]["R"] < 0.05  # the method against exact line integrals of the same interpolant
+    assert abs(out["a"]["R"] - out["b"]["R"]) < 1e-5 and abs(out["a"]["R#"] - out["b"]["R#"]) < 1e-5
+    assert "8 angles x 16 live bins" in out["sample"]
