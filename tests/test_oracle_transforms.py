@@ -216,3 +216,52 @@ def test_planted_mistakes_fail_the_forward_pin(monkeypatch, mistake):
         monkeypatch.setattr(kernels, "full_grid", lambda q, a, b: np.roll(orig(q, a, b), 1, axis=1))
     bad = _forward_err(geo)
     assert bad > 20 * base
+
+
+# ---------------------------------------------------------------- symmetries and special cases
+
+def test_logpolar_forward_of_the_constant_disc_is_the_chord_length():
+    """f = 1 on the pixels inside the unit disc: R f(theta, s) -> 2 sqrt(1 - s^2) for every
+    theta (Section 1), at first order in the pixel size (the disc's edge is a jump)."""
+    errs = []
+    for N in (64, 128):
+        geo = geometry.make_geometry(N, N, 3 * N // 2, 3)
+        Rf = logpolar.forward(np.ones((N, N)), geo)
+        s = (np.arange(geo.n_det) - geo.n_det / 2) * geo.ds
+        chord = np.where(np.abs(s) < 1, 2 * np.sqrt(np.clip(1 - s * s, 0, None)), 0.0)
+        errs.append(_rel(Rf, np.broadcast_to(chord, Rf.shape)))
+    assert errs[1] < 1e-2
+    assert math.log2(errs[0] / errs[1]) > 0.8
+
+
+def test_logpolar_forward_mirror_symmetry():
+    """f(-x1, x2) has R f(pi - theta, s): angle a -> n_angles - a, and angle 0 -> angle 0 with
+    s -> -s (bin k -> n_det - k); pixel column j -> N - j.  The partitions' half-open angle ranges
+    are not mirror images, so the identity holds to the method's error, which falls like h^4; a
+    sign or half-bin slip in theta, s or T_m would break it at O(1)."""
+    errs = []
+    for N in (64, 128):
+        geo = geometry.make_geometry(N, N, 3 * N // 2, 3)
+        f = gaussian_image(N, BLOBS)
+        fm = np.zeros_like(f)
+        fm[:, 1:] = f[:, :0:-1]
+        R = logpolar.forward(f, geo)
+        expect = np.zeros_like(R)
+        expect[1:] = R[:0:-1]
+        expect[0, 1:] = R[0, :0:-1]
+        errs.append(_rel(logpolar.forward(fm, geo), expect))
+    assert errs[1] < 2e-5
+    assert math.log2(errs[0] / errs[1]) > 3.0
+
+
+def test_logpolar_transforms_are_linear():
+    N = 48
+    geo = geometry.make_geometry(N, 40, 72, 3)
+    rng = np.random.default_rng(12)
+    f1, f2 = rng.standard_normal((2, N, N))
+    g1, g2 = rng.standard_normal((2, 40, 72))
+    a, b = 0.7, -1.9
+    R = logpolar.forward
+    assert _rel(R(a * f1 + b * f2, geo), a * R(f1, geo) + b * R(f2, geo)) < 1e-13
+    B = logpolar.backproject
+    assert _rel(B(a * g1 + b * g2, geo), a * B(g1, geo) + b * B(g2, geo)) < 1e-13
