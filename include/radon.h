@@ -161,8 +161,8 @@ int radon_kernel_quadrant(int N, int n_angles, int n_det, int n_partitions, int 
  * convolution, 3 forward inverse rho FFT, 4 sinogram gather, 5 sinogram pre-filter,
  * 6 back-projection row sampling + rho FFT, 7 back-projection theta convolution,
  * 8 back-projection inverse rho FFT, 9 image gather, 10 FBP filter along s, 11 forward row
- * sampling (log-polar resampling of the image); radon_transpose: 12 scatter of the sinogram
- * onto the log-polar grid, 13 rho FFT, 14 transposed theta convolution, 15 inverse rho FFT,
+ * sampling (log-polar resampling of the image); radon_transpose: 12 clearing of the scatter
+ * targets and scatter of the sinogram onto the log-polar grid, 13 rho FFT, 14 transposed theta convolution, 15 inverse rho FFT,
  * 16 scatter onto the image coefficients, 17 Q^T and the disc mask. */
 #define RADON_NUM_STAGES 18
 int radon_profile_enable(radon_plan plan, int enable);
