@@ -50,24 +50,63 @@ void hilo(double v, float* hi, float* lo) {
   *lo = static_cast<float>(v - static_cast<double>(*hi));
 }
 
-// In-place iterative radix-2 FFT, forward sign (exp(-2 pi i jk/n)), n a power of two.
-void fft_pow2(std::vector<cd>& a, const std::vector<cd>& w /* n/2 twiddles */) {
-  const size_t n = a.size();
-  for (size_t i = 1, j = 0; i < n; ++i) {
-    size_t bit = n >> 1;
-    for (; j & bit; bit >>= 1) j ^= bit;
-    j ^= bit;
-    if (i < j) std::swap(a[i], a[j]);
+cd cmul_plain(const cd& x, const cd& y) {  // plain complex product (no inf/NaN recovery path)
+  return cd(x.real() * y.real() - x.imag() * y.imag(), x.real() * y.imag() + x.imag() * y.real());
+}
+
+// Out-of-place Stockham FFT, forward sign (exp(-2 pi i jk/n)), n a power of two, tw[k] =
+// exp(-2 pi i k / n) for k < n: one radix-2 pass when log2 n is odd, then radix-4 passes.
+// Ping-pongs between a and b; returns the buffer holding the result.
+cd* fft_pow2(cd* a, cd* b, size_t n, const cd* tw) {
+  size_t ns = 1;
+  size_t lg = 0;
+  while ((size_t(1) << lg) < n) ++lg;
+  if (lg & 1) {
+    for (size_t j = 0; j < n / 2; ++j) {
+      const cd u = a[j], v = a[j + n / 2];
+      b[2 * j] = u + v;
+      b[2 * j + 1] = u - v;
+    }
+    std::swap(a, b);
+    ns = 2;
   }
-  for (size_t len = 2; len <= n; len <<= 1) {
-    const size_t step = n / len;
-    for (size_t i = 0; i < n; i += len)
-      for (size_t k = 0; k < len / 2; ++k) {
-        cd u = a[i + k];
-        cd v = a[i + k + len / 2] * w[k * step];
-        a[i + k] = u + v;
-        a[i + k + len / 2] = u - v;
-      }
+  const size_t q = n / 4;
+  for (; ns < n; ns *= 4) {
+    const size_t ts = n / (4 * ns);
+    for (size_t j = 0; j < q; ++j) {
+      const size_t k = j & (ns - 1);
+      const cd x0 = a[j];
+      const cd x1 = cmul_plain(a[j + q], tw[k * ts]);
+      const cd x2 = cmul_plain(a[j + 2 * q], tw[2 * k * ts]);
+      const cd x3 = cmul_plain(a[j + 3 * q], tw[3 * k * ts]);
+      const cd t0 = x0 + x2, t1 = x0 - x2, t2 = x1 + x3, d = x1 - x3;
+      const cd t3(d.imag(), -d.real());  // -i (x1 - x3)
+      cd* o = b + 4 * (j - k) + k;
+      o[0] = t0 + t2;
+      o[ns] = t1 + t3;
+      o[2 * ns] = t0 - t2;
+      o[3 * ns] = t1 - t3;
+    }
+    std::swap(a, b);
+  }
+  return a;
+}
+
+// The first nk bins of the length-n DFT of a (n = P Q, nk <= Q, both powers of two), by
+// splitting the sum over j = m P + p into P interleaved length-Q DFTs:
+//   out[k] = sum_p exp(-2 pi i p k / n) DFT_Q(a[p], a[p + P], ...)[k].
+// at holds a regrouped as at[p Q + m] = a[m P + p] and is overwritten; scratch holds Q values.
+void dft_first_bins(cd* at, cd* scratch, size_t n, size_t Q, size_t nk, const cd* tw_n, const cd* tw_q, cd* out) {
+  const size_t P = n / Q;
+  for (size_t k = 0; k < nk; ++k) out[k] = 0.0;
+  for (size_t p = 0; p < P; ++p) {
+    const cd* B = fft_pow2(at + p * Q, scratch, Q, tw_q);
+    size_t idx = 0;  // p k mod n
+    for (size_t k = 0; k < nk; ++k) {
+      out[k] += cmul_plain(tw_n[idx], B[k]);
+      idx += p;
+      if (idx >= n) idx -= n;
+    }
   }
 }
 
@@ -157,33 +196,46 @@ void kernel_quadrant(const radon_plan_info& g, int which, std::vector<double>* o
   out->assign(2 * static_cast<size_t>(nkt) * nkr, 0.0);
   const double h = 2.0 * g.beta / nq;
   const double nu = 2.0 * kPi / g.L;
-  std::vector<double> lc(nq), wq(nq, 1.0);
-  for (int n = 0; n < nq; ++n) lc[n] = std::log(std::cos(-g.beta + n * h));
-  wq[0] += 2.0 * c[0] / 120960.0;
+  // Only the first nkt DFT bins are needed (nkt << nq): dft_first_bins splits the sum into P
+  // interleaved DFTs of length Q.  The per-node arrays are stored regrouped for it (node
+  // n = m P + p at index p Q + m), so every pass over the nodes below is sequential.
+  size_t Q = 1;
+  while (Q < static_cast<size_t>(nkt)) Q <<= 1;
+  const size_t P = nq / Q;
+  std::vector<double> w(nq, 1.0);
+  w[0] += 2.0 * c[0] / 120960.0;
   for (int j = 1; j < 7; ++j) {
-    wq[j] += c[j] / 120960.0;
-    wq[nq - j] += c[j] / 120960.0;
+    w[j] += c[j] / 120960.0;
+    w[nq - j] += c[j] / 120960.0;
   }
-  std::vector<cd> tw(nq / 2);
-  for (int k = 0; k < nq / 2; ++k) tw[k] = std::polar(1.0, -2.0 * kPi * k / nq);
-  // exp(alpha(k_rho) log cos theta_n) is stepped in k_rho by the factor exp(-+ i nu log cos theta_n)
-  // and recomputed directly every 64 steps.
   const double sgn = which == 0 ? -1.0 : 1.0;
-  std::vector<cd> step(nq);
-  for (int n = 0; n < nq; ++n) step[n] = std::polar(1.0, sgn * nu * lc[n]);
+  std::vector<double> lc(nq), wq(nq);  // log cos(theta_n) and the corrected weights, regrouped
+  std::vector<cd> step(nq);            // exp(-+ i nu log cos theta_n), regrouped
+  for (size_t p = 0; p < P; ++p)
+    for (size_t m = 0; m < Q; ++m) {
+      const size_t n = m * P + p, i = p * Q + m;
+      lc[i] = std::log(std::cos(-g.beta + static_cast<double>(n) * h));
+      wq[i] = w[n];
+      step[i] = std::polar(1.0, sgn * nu * lc[i]);
+    }
+  std::vector<cd> tw(nq), tw_q(Q);
+  for (int k = 0; k < nq; ++k) tw[k] = std::polar(1.0, -2.0 * kPi * k / nq);
+  for (size_t k = 0; k < Q; ++k) tw_q[k] = std::polar(1.0, -2.0 * kPi * static_cast<double>(k) / Q);
+  // exp(alpha(k_rho) log cos theta_n) is stepped in k_rho by the factor step[n] and recomputed
+  // directly every 64 steps.
   parallel_for(nkr, [&](int b, int e) {
-    std::vector<cd> a(nq), cur(nq);
+    std::vector<cd> cur(nq), at(nq), scratch(Q), bins(nkt);
     for (int kr = b; kr < e; ++kr) {
       if ((kr - b) % 64 == 0) {
         const cd alpha = which == 0 ? cd(-1.0, -nu * kr) : cd(0.0, nu * kr);
         for (int n = 0; n < nq; ++n) cur[n] = std::exp(alpha * lc[n]);
       } else {
-        for (int n = 0; n < nq; ++n) cur[n] *= step[n];
+        for (int n = 0; n < nq; ++n) cur[n] = cmul_plain(cur[n], step[n]);
       }
-      for (int n = 0; n < nq; ++n) a[n] = cur[n] * wq[n];
-      fft_pow2(a, tw);
+      for (int n = 0; n < nq; ++n) at[n] = cur[n] * wq[n];
+      dft_first_bins(at.data(), scratch.data(), nq, Q, nkt, tw.data(), tw_q.data(), bins.data());
       for (int kt = 0; kt < nkt; ++kt) {
-        const cd v = a[kt] * (h * ((kt & 1) ? -1.0 : 1.0));
+        const cd v = bins[kt] * (h * ((kt & 1) ? -1.0 : 1.0));
         (*out)[2 * (static_cast<size_t>(kt) * nkr + kr)] = v.real();
         (*out)[2 * (static_cast<size_t>(kt) * nkr + kr) + 1] = v.imag();
       }
