@@ -92,18 +92,29 @@ cd* fft_pow2(cd* a, cd* b, size_t n, const cd* tw) {
   return a;
 }
 
-// The first nk bins of the length-n DFT of a (n = P Q, nk <= Q, both powers of two), by
-// splitting the sum over j = m P + p into P interleaved length-Q DFTs:
-//   out[k] = sum_p exp(-2 pi i p k / n) DFT_Q(a[p], a[p + P], ...)[k].
-// at holds a regrouped as at[p Q + m] = a[m P + p] and is overwritten; scratch holds Q values.
-void dft_first_bins(cd* at, cd* scratch, size_t n, size_t Q, size_t nk, const cd* tw_n, const cd* tw_q, cd* out) {
-  const size_t P = n / Q;
+// The first nk bins of the length-n DFT of a sequence with a[n - j] = a[j] (indices mod n),
+// n = P Q with nk <= Q and P >= 2 powers of two.  Splitting j = m P + p into P interleaved
+// subsequences s_p gives out[k] = sum_p w^(p k) DFT_Q(s_p)[k], w = exp(-2 pi i / n).  The
+// symmetry maps s_(P-p)[m] to s_p[Q-1-m], so DFT_Q(s_(P-p))[k] = w^(-P k) DFT_Q(s_p)[Q-k] and
+// only s_0 ... s_(P/2) are transformed:
+//   out[k] = B_0[k] + sum_(0<p<P/2) (w^(p k) B_p[k] + w^(-p k) B_p[(Q-k) mod Q]) + w^(P k/2) B_(P/2)[k].
+// at holds s_0 ... s_(P/2) back to back (at[p Q + m] = a[m P + p]) and is overwritten; scratch
+// holds Q values.
+void dft_first_bins_even(cd* at, cd* scratch, size_t n, size_t Q, size_t nk, const cd* tw_n, const cd* tw_q,
+                         cd* out) {
+  const size_t P = n / Q, half = P / 2;
   for (size_t k = 0; k < nk; ++k) out[k] = 0.0;
-  for (size_t p = 0; p < P; ++p) {
+  for (size_t p = 0; p <= half; ++p) {
     const cd* B = fft_pow2(at + p * Q, scratch, Q, tw_q);
     size_t idx = 0;  // p k mod n
     for (size_t k = 0; k < nk; ++k) {
-      out[k] += cmul_plain(tw_n[idx], B[k]);
+      const cd w = tw_n[idx];
+      if (p == 0)
+        out[k] += B[k];
+      else if (p == half)
+        out[k] += cmul_plain(w, B[k]);
+      else
+        out[k] += cmul_plain(w, B[k]) + cmul_plain(std::conj(w), B[(Q - k) & (Q - 1)]);
       idx += p;
       if (idx >= n) idx -= n;
     }
@@ -196,12 +207,14 @@ void kernel_quadrant(const radon_plan_info& g, int which, std::vector<double>* o
   out->assign(2 * static_cast<size_t>(nkt) * nkr, 0.0);
   const double h = 2.0 * g.beta / nq;
   const double nu = 2.0 * kPi / g.L;
-  // Only the first nkt DFT bins are needed (nkt << nq): dft_first_bins splits the sum into P
-  // interleaved DFTs of length Q.  The per-node arrays are stored regrouped for it (node
-  // n = m P + p at index p Q + m), so every pass over the nodes below is sequential.
+  // Only the first nkt DFT bins are needed (nkt << nq), and the integrand is even in theta, so the
+  // node sequence is symmetric (node nq - n is -theta_n, same weight): dft_first_bins_even
+  // transforms the interleaved subsequences p = 0 ... P/2 only.  The per-node arrays hold those
+  // nodes regrouped for it (node n = m P + p at index p Q + m), so every pass below is sequential.
   size_t Q = 1;
   while (Q < static_cast<size_t>(nkt)) Q <<= 1;
   const size_t P = nq / Q;
+  const int nh_nodes = static_cast<int>((P / 2 + 1) * Q);
   std::vector<double> w(nq, 1.0);
   w[0] += 2.0 * c[0] / 120960.0;
   for (int j = 1; j < 7; ++j) {
@@ -209,9 +222,9 @@ void kernel_quadrant(const radon_plan_info& g, int which, std::vector<double>* o
     w[nq - j] += c[j] / 120960.0;
   }
   const double sgn = which == 0 ? -1.0 : 1.0;
-  std::vector<double> lc(nq), wq(nq);  // log cos(theta_n) and the corrected weights, regrouped
-  std::vector<cd> step(nq);            // exp(-+ i nu log cos theta_n), regrouped
-  for (size_t p = 0; p < P; ++p)
+  std::vector<double> lc(nh_nodes), wq(nh_nodes);  // log cos(theta_n), corrected weights (regrouped)
+  std::vector<cd> step(nh_nodes);                  // exp(-+ i nu log cos theta_n) (regrouped)
+  for (size_t p = 0; p <= P / 2; ++p)
     for (size_t m = 0; m < Q; ++m) {
       const size_t n = m * P + p, i = p * Q + m;
       lc[i] = std::log(std::cos(-g.beta + static_cast<double>(n) * h));
@@ -224,16 +237,16 @@ void kernel_quadrant(const radon_plan_info& g, int which, std::vector<double>* o
   // exp(alpha(k_rho) log cos theta_n) is stepped in k_rho by the factor step[n] and recomputed
   // directly every 64 steps.
   parallel_for(nkr, [&](int b, int e) {
-    std::vector<cd> cur(nq), at(nq), scratch(Q), bins(nkt);
+    std::vector<cd> cur(nh_nodes), at(nh_nodes), scratch(Q), bins(nkt);
     for (int kr = b; kr < e; ++kr) {
       if ((kr - b) % 64 == 0) {
         const cd alpha = which == 0 ? cd(-1.0, -nu * kr) : cd(0.0, nu * kr);
-        for (int n = 0; n < nq; ++n) cur[n] = std::exp(alpha * lc[n]);
+        for (int n = 0; n < nh_nodes; ++n) cur[n] = std::exp(alpha * lc[n]);
       } else {
-        for (int n = 0; n < nq; ++n) cur[n] = cmul_plain(cur[n], step[n]);
+        for (int n = 0; n < nh_nodes; ++n) cur[n] = cmul_plain(cur[n], step[n]);
       }
-      for (int n = 0; n < nq; ++n) at[n] = cur[n] * wq[n];
-      dft_first_bins(at.data(), scratch.data(), nq, Q, nkt, tw.data(), tw_q.data(), bins.data());
+      for (int n = 0; n < nh_nodes; ++n) at[n] = cur[n] * wq[n];
+      dft_first_bins_even(at.data(), scratch.data(), nq, Q, nkt, tw.data(), tw_q.data(), bins.data());
       for (int kt = 0; kt < nkt; ++kt) {
         const cd v = bins[kt] * (h * ((kt & 1) ? -1.0 : 1.0));
         (*out)[2 * (static_cast<size_t>(kt) * nkr + kr)] = v.real();
