@@ -62,7 +62,8 @@ def test_invalid_geometry_is_rejected(lib):
             lib.radon_geometry(*args)
 
 
-@pytest.mark.parametrize("N,na,nd,M", [(64, 64, 96, 3), (128, 128, 192, 3), (256, 256, 384, 4)])
+@pytest.mark.parametrize("N,na,nd,M", [(64, 64, 96, 3), (128, 128, 192, 3), (256, 256, 384, 4),
+                                       (16, 5, 20, 3), (16, 12, 24, 3), (64, 37, 90, 5)])
 def test_plan_kernel_transforms_match_oracle(lib, N, na, nd, M):
     o = geometry.make_geometry(N, na, nd, M)
     for which, key in ((0, "R"), (1, "B")):
