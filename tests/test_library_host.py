@@ -84,3 +84,22 @@ def test_end_correction_weights_are_exact_to_degree_six():
     expect = [0.0, 1 / 12, 0.0, -factorial(3) / 720, 0.0, factorial(5) / 30240, 0.0]
     for p in range(7):
         assert np.sum(c * j**p) / 120960 == pytest.approx(expect[p], abs=1e-15)
+
+
+def test_every_entry_point_rejects_null_arguments_without_a_gpu(lib):
+    """The C ABI's argument checks run before any CUDA call: a NULL plan or pointer returns
+    RADON_INVALID_ARG (1) from every entry point, with or without a device."""
+    cdll = lib.load()
+    for name in ("radon_forward", "radon_backproject", "radon_transpose", "radon_forward_host",
+                 "radon_backproject_host", "radon_forward_static_scratch"):
+        assert getattr(cdll, name)(None, None, None, None) == 1, name
+    for name in ("radon_forward_batch", "radon_backproject_batch", "radon_transpose_batch"):
+        assert getattr(cdll, name)(None, None, None, 1, None) == 1, name
+    assert cdll.radon_fbp(None, None, None, 0, None) == 1
+    assert cdll.radon_plan_kernel_launches(None, 3, None) == 1
+    assert cdll.radon_plan_reserve_batch(None, 2) == 1
+    assert cdll.radon_plan_set_column_group(None, 1) == 1
+    assert cdll.radon_profile_enable(None, 1) == 1
+    assert cdll.radon_profile_read(None, None, None) == 1
+    assert cdll.radon_plan_get_info(None, None) == 1
+    assert cdll.radon_status_string(1) == b"invalid argument"
