@@ -160,6 +160,77 @@ def test_logpolar_backprojection_of_gaussian_sinogram(M):
     assert math.log2(errs[0] / errs[1]) > 3.0
 
 
+@pytest.mark.parametrize("M", [3, 5])
+def test_logpolar_backprojection_linear_variant_second_order(M):
+    """Linear variant of Algorithm 2 (raw samples, bilinear weights, multiplier zeta#-hat without
+    B-hat) on the analytic sinogram of Gaussians: R# converges to sum_k w sqrt(2 pi) s pi e^{-u}
+    I_0(u) at second order, the order of linear interpolation."""
+    errs = []
+    for N in (64, 128):
+        geo = geometry.make_geometry(N, N, 3 * N // 2, M, interp=1)
+        errs.append(_rel(logpolar.backproject(_analytic_gauss_sino(geo), geo), _gauss_bp_image(geo)))
+    assert errs[1] < 3e-3
+    assert math.log2(errs[0] / errs[1]) > 1.8
+
+
+ISOLATED = [[(0.0, 0.0, 0.2, 1.0)], [(0.2, -0.1, 0.15, 1.0)], [(-0.3, 0.3, 0.1, 1.0)]]
+
+
+@pytest.mark.parametrize("blobs", ISOLATED)
+def test_logpolar_backprojection_linear_variant_lowers_smooth_maxima(blobs):
+    """Every resampling of the linear variant uses nonnegative weights that reproduce affine
+    functions, so by Jensen's inequality it never exceeds a locally concave function; the
+    convolution integrates along the curves rho = log cos theta with a positive weight.  At the
+    maximum of an isolated Gaussian's back-projection the result therefore falls short of the
+    closed form, by an amount that shrinks like h^2.  A sharpening step (such as dividing the
+    linear multiplier by B-hat, which belongs to the cubic variant) overshoots instead."""
+    defs = []
+    for N in (64, 128):
+        geo = geometry.make_geometry(N, N, 3 * N // 2, 3, interp=1)
+        ref = _gauss_bp_image(geo, blobs)
+        got = logpolar.backproject(_analytic_gauss_sino(geo, blobs), geo)
+        i = np.unravel_index(np.argmax(ref), ref.shape)
+        defs.append((got[i] - ref[i]) / ref[i])
+    assert defs[0] < 0 and defs[1] < 0, defs
+    assert 3.0 < defs[0] / defs[1] < 5.5, defs
+
+
+@pytest.mark.parametrize("mistake", ["conj_kernel", "s_tap_shift", "theta_tap_shift", "bhat_in_linear"])
+def test_planted_mistakes_fail_the_linear_backprojection_pins(monkeypatch, mistake):
+    """Each planted mistake in the linear R# must break one of the two pins above: the error
+    against the closed form grows by at least 5x, or the peak deficit changes sign."""
+    N = 128
+    geo = geometry.make_geometry(N, N, 3 * N // 2, 3, interp=1)
+    g, ref = _analytic_gauss_sino(geo), _gauss_bp_image(geo)
+    base = _rel(logpolar.backproject(g, geo), ref)
+    orig_interp = bspline.interp2d
+
+    def shifted(axis):
+        def f(c, t0, t1, order=3, mode0="zero", mode1="zero"):
+            if mode0 == "periodic" and mode1 == "zero":    # the sinogram gather of Algorithm 2
+                t0, t1 = (t0 + 1, t1) if axis == 0 else (t0, t1 + 1)
+            return orig_interp(c, t0, t1, order, mode0, mode1)
+        return f
+
+    if mistake == "conj_kernel":
+        orig = kernels.kernel_quadrant
+        monkeypatch.setattr(kernels, "kernel_quadrant", lambda gg, w, **kw: np.conj(orig(gg, w, **kw)))
+    elif mistake == "s_tap_shift":
+        monkeypatch.setattr(bspline, "interp2d", shifted(1))
+    elif mistake == "theta_tap_shift":
+        monkeypatch.setattr(bspline, "interp2d", shifted(0))
+    elif mistake == "bhat_in_linear":
+        orig_mult = kernels.multiplier
+        monkeypatch.setattr(kernels, "multiplier", lambda gg, w: orig_mult(gg, w) / kernels.bhat2d(
+            gg.n_theta, gg.N_rho))
+    bad = _rel(logpolar.backproject(g, geo), ref)
+    blobs = ISOLATED[0]
+    gi, ri = _analytic_gauss_sino(geo, blobs), _gauss_bp_image(geo, blobs)
+    i = np.unravel_index(np.argmax(ri), ri.shape)
+    deficit = logpolar.backproject(gi, geo)[i] - ri[i]
+    assert bad > 5 * base or deficit > 0, (bad, base, deficit)
+
+
 def test_logpolar_forward_conserves_mass_and_centre_per_angle():
     """Fourier slice theorem at sigma = 0 and its first moment: int R f ds = int f and
     int s R f ds = theta . int x f, for every angle."""
