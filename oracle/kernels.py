@@ -61,16 +61,19 @@ def _nodes(edges):
     return t, wt
 
 
-def kernel_quadrant(geo, which: str, phase_per_panel: float = 10.0, chunk: int = 512):
+def kernel_quadrant(geo, which: str, phase_per_panel: float = 10.0, chunk: int = 512, kr_cols=None):
     """zeta_hat (which='R') or zeta#_hat (which='B') for kt in [0, n_theta/2], kr in [0, N_rho/2].
 
-    Returns a complex128 array of shape (n_theta/2 + 1, N_rho/2 + 1).
+    Returns a complex128 array of shape (n_theta/2 + 1, N_rho/2 + 1), or of shape
+    (n_theta/2 + 1, len(kr_cols)) when only the columns ``kr_cols`` are asked for (the panels
+    are the same in both cases: they resolve the fastest oscillation of the whole quadrant).
     """
     beta, L = geo.beta, geo.L
     nu = 2.0 * math.pi / L
     kt = np.arange(geo.n_theta // 2 + 1)
-    kr = np.arange(geo.N_rho // 2 + 1)
-    edges = _panels(math.pi * kt[-1] / beta, nu * kr[-1], beta, phase_per_panel)
+    kr_max = geo.N_rho // 2
+    kr = np.arange(kr_max + 1) if kr_cols is None else np.asarray(kr_cols, dtype=np.int64)
+    edges = _panels(math.pi * kt[-1] / beta, nu * kr_max, beta, phase_per_panel)
     t, w = _nodes(edges)
     lc = np.log(np.cos(t))
     # A[kt, q] = 2 w_q cos(pi t_q kt / beta) (cos t_q)^{-1 or 0}

@@ -73,6 +73,23 @@ def test_plan_kernel_transforms_match_oracle(lib, N, na, nd, M):
         assert np.max(np.abs(plan_k - ref)) < 1e-8 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("N,na,nd,M", [(2048, 2048, 3072, 3), (1024, 720, 1536, 3), (4096, 4096, 6144, 3)])
+def test_plan_kernel_transforms_match_oracle_at_full_size(lib, N, na, nd, M):
+    """The plan's kernel tables at the full single-slice sizes (n_quad = 2^17 trapezoid nodes at
+    N = 2048, pruned to the needed DFT bins over interleaved subsequences) against the oracle's
+    Gauss-Legendre values on a seeded subset of k_rho columns: every k_theta, the first and last
+    columns, and 40 random ones."""
+    o = geometry.make_geometry(N, na, nd, M)
+    rng = np.random.default_rng(2048)
+    kmax = o.N_rho // 2
+    cols = np.unique(np.concatenate([[0, 1, 2, kmax - 1, kmax], rng.integers(0, kmax + 1, 40)]))
+    for which, key in ((0, "R"), (1, "B")):
+        plan_k = lib.radon_kernel_quadrant(N, na, nd, M, which)
+        assert plan_k.shape == (o.n_theta // 2 + 1, kmax + 1)
+        ref = kernels.kernel_quadrant(o, key, kr_cols=cols)
+        assert np.max(np.abs(plan_k[:, cols] - ref)) < 1e-8 * np.max(np.abs(ref)), key
+
+
 def test_end_correction_weights_are_exact_to_degree_six():
     """Eq. weightsa: with f(a + j h) the moments sum_j c_j j^p / 120960 equal the
     Euler-Maclaurin end terms 0, 1/12, 0, -1/720 * 3!, 0, 1/30240 * 5!, 0."""
