@@ -19,6 +19,7 @@
 // Every gather clamps its tap indices into the buffer it reads.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 
 #include "plan_host.h"
@@ -386,6 +387,8 @@ __device__ __forceinline__ float sample_image(const DevPlan& p, int b, int ic, f
 // a CTA holds the same tile of kSampleWarps adjacent rows, so its taps overlap in L1.  The real row h is written to the
 // spectrum scratch yspec (free until the theta convolution), 2 x_pitch floats per row.
 constexpr int kSampleWarps = 8;
+// Image sizes N whose forward sampling is compiled with a constant padded pitch N + 2 kPad.
+#define RADON_SAMPLE_PITCHES(X) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
 
 
 // Cubic B-spline weights times 6 (the 1/36 of a 2-D tap block is applied once per output) for
@@ -403,8 +406,10 @@ __device__ __forceinline__ void bspline_w6_pair(float2 a, float2 (&w)[4]) {
 
 // Two rho samples per thread (i and i + 32, tiles 2 blockIdx.x and 2 blockIdx.x + 1) for each
 // sub-angle q; a sample is read only when i lies in the sub-angle's range fwd_rng (its taps are
-// then inside the padded array), so no per-sample bounds test is needed.
-template <bool QUAD>
+// then inside the padded array), so no per-sample bounds test is needed.  PITCH > 0 fixes the
+// padded image width at compile time (the tabulated sizes N = PITCH - 2 kPad): a tap block's four
+// quad rows are then one address plus constant offsets.
+template <bool QUAD, int PITCH = 0>
 __global__ void __launch_bounds__(kSampleWarps * 32) k_sample_fwd(DevPlan p) {
   extern __shared__ __align__(16) float4 sanc[];  // [warp][2][q] anchors, [warp][q] directions, [warp][q] ranges
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -439,7 +444,7 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_sample_fwd(DevPlan p) {
   const int i0 = base + lane, i1 = i0 + kETile;
   const float2 e0 = i0 < p.N_rho ? p.fwd_e[i0] : make_float2(0.f, 0.f);
   const float2 e1 = i1 < p.N_rho ? p.fwd_e[i1] : make_float2(0.f, 0.f);
-  const int P = p.img_pitch;
+  const int P = PITCH > 0 ? PITCH : p.img_pitch;
   float acc0 = 0.f, acc1 = 0.f;
   for (int q = 0; q < r; ++q) {
     const int2 rg = rng[q];
@@ -455,13 +460,25 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_sample_fwd(DevPlan p) {
     const int ic1 = ok1 ? static_cast<int>(a1.x + fc1) : 1, ir1 = ok1 ? static_cast<int>(a1.z + fr1) : 1;
     if constexpr (QUAD) {
       const float4* __restrict__ img = p.coef_q4 + b * p.bs_img;
-      const float4* p0 = img + static_cast<size_t>(ir0 - 1) * P + (ic0 - 1);
-      const float4* p1 = img + static_cast<size_t>(ir1 - 1) * P + (ic1 - 1);
       float4 v0[4], v1[4];
+      if constexpr (PITCH > 0) {
+        // 32-bit element offsets (the padded image has fewer than 2^31 elements); the rows of a
+        // tap block are constant offsets from its first element
+        const float4* p0 = img + static_cast<unsigned>(ir0 * PITCH + ic0) - (PITCH + 1);
+        const float4* p1 = img + static_cast<unsigned>(ir1 * PITCH + ic1) - (PITCH + 1);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        v0[k] = __ldg(p0 + k * P);
-        v1[k] = __ldg(p1 + k * P);
+        for (int k = 0; k < 4; ++k) {
+          v0[k] = __ldg(p0 + k * PITCH);
+          v1[k] = __ldg(p1 + k * PITCH);
+        }
+      } else {
+        const float4* p0 = img + static_cast<size_t>(ir0 - 1) * P + (ic0 - 1);
+        const float4* p1 = img + static_cast<size_t>(ir1 - 1) * P + (ic1 - 1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          v0[k] = __ldg(p0 + k * P);
+          v1[k] = __ldg(p1 + k * P);
+        }
       }
       float2 wc[4], wr[4];  // .x: sample i0, .y: sample i1
       bspline_w6_pair(make_float2(Fc0 - fc0, Fc1 - fc1), wc);
@@ -841,6 +858,121 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Persistent row transforms.  One CTA per resident slot walks the rows R = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the twiddle table is staged once per CTA, and while row R is
+// transformed the next row is already being copied into the other staging buffer with cp.async
+// (16-byte asynchronous copies that bypass the registers), so the load latency that stalls the
+// one-row-per-CTA kernels overlaps the FFT.  Results equal those of k_rows_fwd<false> /
+// k_rows_inv bit for bit (same arithmetic in the same order).
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Shared-memory layout of the persistent row kernels (float2 entries): twiddles (nc, rounded up
+// to even), two staging buffers of x_pitch entries, one work buffer of nc.
+__host__ __device__ __forceinline__ int rows_pipe_stage0(const DevPlan& p) { return (p.nc + 1) & ~1; }
+
+// Copy the first 16-byte chunks [0, chunks) of a spectrum-scratch row into shared memory.
+__device__ __forceinline__ void prefetch_row(float2* dst, const float2* __restrict__ src, int chunks) {
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) cp_async16(dst + 2 * c, src + 2 * c);
+}
+
+// Forward: the rows k_sample_fwd wrote (n_rows = M nh per slice, batch slices), real FFT along
+// rho, half spectrum to xspec.
+template <int SEQ>
+__global__ void __launch_bounds__(kThreads) k_rows_fwd_pipe(DevPlan p, int n_rows) {
+  extern __shared__ __align__(16) float2 smem[];
+  const int nc = p.nc, s0 = rows_pipe_stage0(p);
+  float2* tws = smem;
+  float2* stg0 = smem + s0;
+  float2* stg1 = stg0 + p.x_pitch;
+  float2* work = stg1 + p.x_pitch;
+  stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
+  const int per_slice = p.M * p.nh, chunks = (nc + 1) / 2;
+  auto src_row = [&](int R) {
+    const int b = R / per_slice;
+    return p.yspec + b * p.bs_ys + static_cast<size_t>(R - b * per_slice) * p.x_pitch;
+  };
+  int R = blockIdx.x;
+  if (R < n_rows) prefetch_row(stg0, src_row(R), chunks);
+  cp_async_commit();
+  for (int it = 0; R < n_rows; R += gridDim.x, ++it) {
+    float2* cur = (it & 1) ? stg1 : stg0;
+    if (R + static_cast<int>(gridDim.x) < n_rows) prefetch_row((it & 1) ? stg0 : stg1, src_row(R + gridDim.x), chunks);
+    cp_async_commit();
+    cp_async_wait_prev();  // this thread's copies of row R have landed
+    __syncthreads();       // and everyone's
+    const float2* Z = row_fft<false, SEQ>(cur, work, p, tws);
+    const int b = R / per_slice;
+    float2* out = p.xspec + b * p.bs_x + static_cast<size_t>(R - b * per_slice) * p.x_pitch;
+    for (int k = threadIdx.x; k <= nc; k += blockDim.x) {
+      const float2 zk = Z[k == nc ? 0 : k];
+      const float2 zc = cconj(Z[k == 0 ? 0 : nc - k]);
+      const float2 ev = cscale(cadd(zk, zc), 0.5f);
+      const float2 dv = cscale(csub(zk, zc), 0.5f);
+      const float2 od = make_float2(dv.y, -dv.x);  // -i (Z_k - conj Z_{n-k}) / 2
+      out[k] = cadd(ev, cmul(p.tw_r2c[k], od));
+    }
+    __syncthreads();  // cur and work are overwritten by the next iteration
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Inverse: the kept rows after the theta convolution (n_rows = M (nh + halo) per slice), inverse
+// real FFT along rho, N_rho values plus kPad wrap columns per side to the log-polar array.
+template <int SEQ>
+__global__ void __launch_bounds__(kThreads) k_rows_inv_pipe(DevPlan p, int n_rows) {
+  extern __shared__ __align__(16) float2 smem[];
+  const int nc = p.nc, nr = p.N_rho, s0 = rows_pipe_stage0(p);
+  float2* tws = smem;
+  float2* stg0 = smem + s0;
+  float2* stg1 = stg0 + p.x_pitch;
+  float2* work = stg1 + p.x_pitch;
+  stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
+  const int nrow = p.nh + kHaloLo + kHaloHi, per_slice = p.M * nrow, chunks = (nc + 2) / 2;
+  auto src_row = [&](int R) {
+    const int b = R / per_slice;
+    return p.yspec + b * p.bs_ys + static_cast<size_t>(R - b * per_slice) * p.x_pitch;
+  };
+  int R = blockIdx.x;
+  if (R < n_rows) prefetch_row(stg0, src_row(R), chunks);
+  cp_async_commit();
+  for (int it = 0; R < n_rows; R += gridDim.x, ++it) {
+    const float2* X = (it & 1) ? stg1 : stg0;
+    if (R + static_cast<int>(gridDim.x) < n_rows) prefetch_row((it & 1) ? stg0 : stg1, src_row(R + gridDim.x), chunks);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      const float2 xk = X[k];
+      const float2 xc = cconj(X[nc - k]);
+      const float2 sm = cadd(xk, xc);
+      const float2 df = cmulc(csub(xk, xc), p.tw_r2c[k]);  // (X_k - conj X_{n-k}) exp(+2 pi i k / N_rho)
+      work[k] = make_float2(sm.x - df.y, sm.y + df.x);       // + i * df
+    }
+    __syncthreads();
+    const float2* Z = row_fft<true, SEQ>(work, const_cast<float2*>(X), p, tws);
+    const float* h = reinterpret_cast<const float*>(Z);
+    const int b = R / per_slice, mr = R - b * per_slice;  // mr = m nrow + row
+    float* y = p.ylp + b * p.bs_y + static_cast<size_t>(mr) * p.y_pitch;
+    const int yrow = b * per_slice + mr;
+    for (int c = static_cast<int>(threadIdx.x) - kPad; c < nr + kPad; c += blockDim.x) {
+      const int src = c < 0 ? c + nr : (c >= nr ? c - nr : c);
+      if (p.use_tex)
+        surf2Dwrite(h[src], p.surf_lp, (c + kPad) * static_cast<int>(sizeof(float)), yrow);
+      else
+        y[c + kPad] = h[src];
+    }
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ------------------------------------------------------------------------------------------
 // Output gathers.
 
 // Interpolant of partition m's log-polar coefficients at (halo row It + at, padded column
@@ -1122,84 +1254,195 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r_t(DevPlan p) {
 // sample adds h(phi_j, rho_i) e^rho_i / r times its tap weights to the padded coefficient image
 // coef_img (zeroed beforehand).  Tap blocks are bounds-checked like sample_image, and taps in the
 // zero border are dropped (the forward reads them as constants), so the border stays zero.
+//
+// The CTA's 8 rays x 64 rho samples x r sub-angles cover a thin wedge of the image (about
+// 40 x 65 pixels at N = 2048).  Their taps are first summed in a shared-memory box over the
+// wedge's bounding rectangle (found by a first pass over the same coordinates), and the box is
+// then added to coef_img with one global atomic per touched pixel: about 30x fewer global atomics
+// than one per tap.  A CTA whose rectangle exceeds kScatterBox floats adds its taps to coef_img
+// directly.
+constexpr int kScatterBox = 10240;  // floats of the per-CTA accumulation box (40 KB)
+
+struct ScatterTap {
+  int ic, ir;
+  float ac, ar;
+};
+
+// Tap-block corner of one fine sample and its fractions; false if the block is out of range.
+__device__ __forceinline__ bool scatter_corner(int interp, const float4& a, float ey, float2 d, int P, ScatterTap& t) {
+  const float Fc = fmaf(ey, d.x, a.y), Fr = fmaf(ey, d.y, a.w);
+  const float fc = floorf(Fc), fr = floorf(Fr);
+  t.ic = static_cast<int>(a.x + fc);
+  t.ir = static_cast<int>(a.z + fr);
+  t.ac = Fc - fc;
+  t.ar = Fr - fr;
+  if (interp == 3) return !(t.ic < 1 || t.ic > P - 3 || t.ir < 1 || t.ir > P - 3);
+  return !(t.ic < 0 || t.ic > P - 2 || t.ir < 0 || t.ir > P - 2);
+}
+
+// Adds the SPAN x SPAN tap block with top-left padded index (rt, ct) and weights wr x wc to the
+// box (origin (r0, c0), W x H) or to coef_img; taps in the zero border are dropped.
+template <int SPAN>
+__device__ __forceinline__ void scatter_block(const float (&wc)[SPAN], const float (&wr)[SPAN], int rt, int ct, int P,
+                                              bool use_box, float* box, int W, int H, int r0, int c0,
+                                              float* __restrict__ img) {
+#pragma unroll
+  for (int dr = 0; dr < SPAN; ++dr) {
+    if (!interior_tap(rt + dr, P)) continue;
+#pragma unroll
+    for (int dc = 0; dc < SPAN; ++dc) {
+      if (!interior_tap(ct + dc, P)) continue;
+      const float val = wr[dr] * wc[dc];
+      if (use_box) {
+        const int by = rt + dr - r0, bx = ct + dc - c0;
+        if (static_cast<unsigned>(by) < static_cast<unsigned>(H) && static_cast<unsigned>(bx) < static_cast<unsigned>(W))
+          atomicAdd(box + by * W + bx, val);
+      } else {
+        atomicAdd(img + static_cast<size_t>(rt + dr) * P + (ct + dc), val);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kSampleWarps * 32) k_scatter_fwd(DevPlan p) {
   extern __shared__ __align__(16) float4 sanc[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = p.r, ne = p.n_eanc;
   const int tile0 = 2 * blockIdx.x, m = blockIdx.z % p.M, b = blockIdx.z / p.M;
   const int jj = blockIdx.y * kSampleWarps + warp;
-  if (jj >= p.nh) return;
+  const bool active = jj < p.nh;  // inactive warps still take part in the CTA barriers
   float4* anc = sanc + warp * 2 * r;
   float2* dir = reinterpret_cast<float2*>(sanc + kSampleWarps * 2 * r) + warp * r;
   int2* rng = reinterpret_cast<int2*>(reinterpret_cast<float2*>(sanc + kSampleWarps * 2 * r) + kSampleWarps * r) + warp * r;
+  float* box = reinterpret_cast<float*>(sanc + kSampleWarps * 3 * r);  // after anchors, directions and ranges
+  int* red = reinterpret_cast<int*>(box + kScatterBox);                 // min col, -max col, min row, -max row
   const float4 um = p.fwd_m[m];
-  const size_t row0 = (static_cast<size_t>(m) * p.nh + jj) * r;
-  const float4* rowc = p.fwd_row + row0;
-  const float2 ea0 = p.fwd_eanc[tile0];
-  const float2 ea1 = p.fwd_eanc[tile0 + 1 < ne ? tile0 + 1 : tile0];
-  for (int q = lane; q < r; q += 32) {
-    const float4 cs = rowc[q];
+  const size_t row0 = (static_cast<size_t>(m) * p.nh + (active ? jj : 0)) * r;
+  if (active) {
+    const float4* rowc = p.fwd_row + row0;
+    const float2 ea0 = p.fwd_eanc[tile0];
+    const float2 ea1 = p.fwd_eanc[tile0 + 1 < ne ? tile0 + 1 : tile0];
+    for (int q = lane; q < r; q += 32) {
+      const float4 cs = rowc[q];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const float2 ea = u ? ea1 : ea0;
-      float ch, cl, rh, rl;
-      df_mul_add(ea.x, ea.y, cs.x, cs.y, um.x, um.y, &ch, &cl);
-      df_mul_add(ea.x, ea.y, cs.z, cs.w, um.z, um.w, &rh, &rl);
-      const float Ic = floorf(ch), Ir = floorf(rh);
-      anc[u * r + q] = make_float4(Ic, (ch - Ic) + cl, Ir, (rh - Ir) + rl);
-    }
-    dir[q] = make_float2(cs.x, cs.z);
-    rng[q] = p.fwd_rng[row0 + q];
-  }
-  __syncwarp();
-  const int base = tile0 * kETile;
-  const int i0 = base + lane, i1 = i0 + kETile;
-  const float* hrow = reinterpret_cast<const float*>(p.yspec + b * p.bs_ys + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch);
-  const float scale = p.interp == 3 ? 1.f / 36.f : 1.f;
-  const float2 e0 = i0 < p.N_rho ? p.fwd_e[i0] : make_float2(0.f, 0.f);
-  const float2 e1 = i1 < p.N_rho ? p.fwd_e[i1] : make_float2(0.f, 0.f);
-  const float v0 = i0 < p.N_rho ? hrow[i0] * e0.x * scale : 0.f;
-  const float v1 = i1 < p.N_rho ? hrow[i1] * e1.x * scale : 0.f;
-  const int P = p.img_pitch;
-  float* __restrict__ img = p.coef_img + b * p.bs_img;
-  for (int q = 0; q < r; ++q) {
-    const int2 rg = rng[q];
-    if (rg.y < base || rg.x > base + 2 * kETile - 1) continue;
-    const float2 d = dir[q];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int i = u ? i1 : i0;
-      const float v = u ? v1 : v0;
-      if (i < rg.x || i > rg.y || v == 0.f) continue;
-      const float4 a = anc[u * r + q];
-      const float ey = u ? e1.y : e0.y;
-      const float Fc = fmaf(ey, d.x, a.y), Fr = fmaf(ey, d.y, a.w);
-      const float fc = floorf(Fc), fr = floorf(Fr);
-      const int ic = static_cast<int>(a.x + fc), ir = static_cast<int>(a.z + fr);
-      if (p.interp == 3) {
-        if (ic < 1 || ic > P - 3 || ir < 1 || ir > P - 3) continue;
-        float2 w[4];  // .x: column weights, .y: row weights (times 6 each)
-        bspline_w6_pair(make_float2(Fc - fc, Fr - fr), w);
-        float* t = img + static_cast<size_t>(ir - 1) * P + (ic - 1);
-#pragma unroll
-        for (int dr = 0; dr < 4; ++dr) {
-          if (!interior_tap(ir - 1 + dr, P)) continue;
-          const float vr = v * w[dr].y;
-#pragma unroll
-          for (int dc = 0; dc < 4; ++dc)
-            if (interior_tap(ic - 1 + dc, P)) atomicAdd(t + dr * P + dc, vr * w[dc].x);
-        }
-      } else {
-        if (ic < 0 || ic > P - 2 || ir < 0 || ir > P - 2) continue;
-        const float ac = Fc - fc, ar = Fr - fr;
-        const float wr[2] = {1.f - ar, ar}, wc[2] = {1.f - ac, ac};
-        float* t = img + static_cast<size_t>(ir) * P + ic;
-#pragma unroll
-        for (int dr = 0; dr < 2; ++dr)
-#pragma unroll
-          for (int dc = 0; dc < 2; ++dc)
-            if (interior_tap(ir + dr, P) && interior_tap(ic + dc, P)) atomicAdd(t + dr * P + dc, v * wr[dr] * wc[dc]);
+      for (int u = 0; u < 2; ++u) {
+        const float2 ea = u ? ea1 : ea0;
+        float ch, cl, rh, rl;
+        df_mul_add(ea.x, ea.y, cs.x, cs.y, um.x, um.y, &ch, &cl);
+        df_mul_add(ea.x, ea.y, cs.z, cs.w, um.z, um.w, &rh, &rl);
+        const float Ic = floorf(ch), Ir = floorf(rh);
+        anc[u * r + q] = make_float4(Ic, (ch - Ic) + cl, Ir, (rh - Ir) + rl);
       }
+      dir[q] = make_float2(cs.x, cs.z);
+      rng[q] = p.fwd_rng[row0 + q];
+    }
+  }
+  if (threadIdx.x == 0) {
+    red[0] = INT_MAX;
+    red[1] = INT_MAX;
+    red[2] = INT_MAX;
+    red[3] = INT_MAX;
+  }
+  __syncthreads();
+  // lane L takes the adjacent samples base + 2L and base + 2L + 1 (both in tile L / 16), so the
+  // 32 lanes of one atomic instruction are two samples apart: fewer of them hit the same pixel
+  const int base = tile0 * kETile;
+  const int i0 = base + 2 * lane, i1 = i0 + 1, tl = lane >> 4;
+  float v0 = 0.f, v1 = 0.f, ey0 = 0.f, ey1 = 0.f;
+  if (active) {
+    const float* hrow = reinterpret_cast<const float*>(p.yspec + b * p.bs_ys + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch);
+    const float scale = p.interp == 3 ? 1.f / 36.f : 1.f;
+    if (i0 < p.N_rho) {
+      const float2 e = p.fwd_e[i0];
+      v0 = hrow[i0] * e.x * scale;
+      ey0 = e.y;
+    }
+    if (i1 < p.N_rho) {
+      const float2 e = p.fwd_e[i1];
+      v1 = hrow[i1] * e.x * scale;
+      ey1 = e.y;
+    }
+  }
+  const int P = p.img_pitch;
+  // pass 1: bounding rectangle of the tap-block corners this CTA scatters to
+  int cmin = INT_MAX, cmax = INT_MIN, rmin = INT_MAX, rmax = INT_MIN;
+  if (active) {
+    for (int q = 0; q < r; ++q) {
+      const int2 rg = rng[q];
+      if (rg.y < base || rg.x > base + 2 * kETile - 1) continue;
+      const float2 d = dir[q];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = u ? i1 : i0;
+        const float v = u ? v1 : v0;
+        if (i < rg.x || i > rg.y || v == 0.f) continue;
+        ScatterTap t;
+        if (!scatter_corner(p.interp, anc[tl * r + q], u ? ey1 : ey0, d, P, t)) continue;
+        cmin = min(cmin, t.ic);
+        cmax = max(cmax, t.ic);
+        rmin = min(rmin, t.ir);
+        rmax = max(rmax, t.ir);
+      }
+    }
+  }
+  cmin = __reduce_min_sync(0xffffffffu, cmin);
+  rmin = __reduce_min_sync(0xffffffffu, rmin);
+  cmax = __reduce_max_sync(0xffffffffu, cmax);
+  rmax = __reduce_max_sync(0xffffffffu, rmax);
+  if (lane == 0 && cmin <= cmax) {
+    atomicMin(red + 0, cmin);
+    atomicMin(red + 1, -cmax);
+    atomicMin(red + 2, rmin);
+    atomicMin(red + 3, -rmax);
+  }
+  __syncthreads();
+  if (red[0] == INT_MAX) return;  // uniform over the CTA: nothing to scatter
+  const int span = p.interp == 3 ? 4 : 2;  // taps per axis
+  const int c0 = red[0] - (p.interp == 3 ? 1 : 0), r0 = red[2] - (p.interp == 3 ? 1 : 0);
+  const int W = -red[1] - red[0] + span, H = -red[3] - red[2] + span;
+  const bool use_box = W * H <= kScatterBox;  // uniform over the CTA
+  float* __restrict__ img = p.coef_img + b * p.bs_img;
+  if (use_box) {
+    for (int idx = threadIdx.x; idx < W * H; idx += blockDim.x) box[idx] = 0.f;
+    __syncthreads();
+  }
+  // pass 2: the taps, into the box or straight into coef_img
+  if (active) {
+    for (int q = 0; q < r; ++q) {
+      const int2 rg = rng[q];
+      if (rg.y < base || rg.x > base + 2 * kETile - 1) continue;
+      const float2 d = dir[q];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = u ? i1 : i0;
+        const float v = u ? v1 : v0;
+        if (i < rg.x || i > rg.y || v == 0.f) continue;
+        ScatterTap t;
+        if (!scatter_corner(p.interp, anc[tl * r + q], u ? ey1 : ey0, d, P, t)) continue;
+        if (p.interp == 3) {
+          float2 w[4];  // .x: column weights, .y: row weights (times 6 each)
+          bspline_w6_pair(make_float2(t.ac, t.ar), w);
+          float wc[4], wr[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            wc[k] = w[k].x;
+            wr[k] = v * w[k].y;
+          }
+          scatter_block<4>(wc, wr, t.ir - 1, t.ic - 1, P, use_box, box, W, H, r0, c0, img);
+        } else {
+          const float wc[2] = {1.f - t.ac, t.ac}, wr[2] = {v * (1.f - t.ar), v * t.ar};
+          scatter_block<2>(wc, wr, t.ir, t.ic, P, use_box, box, W, H, r0, c0, img);
+        }
+      }
+    }
+  }
+  if (!use_box) return;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < W * H; idx += blockDim.x) {
+    const float v = box[idx];
+    if (v != 0.f) {
+      const int by = idx / W, bx = idx - by * W;
+      atomicAdd(img + static_cast<size_t>(r0 + by) * P + (c0 + bx), v);
     }
   }
 }
@@ -1262,14 +1505,32 @@ size_t filt_smem(const DevPlan& p) {
 size_t rows_smem(const DevPlan& p) {
   return (2 + (p.rows_tw_smem ? 1 : 0)) * static_cast<size_t>(p.nc) * sizeof(float2);
 }
+size_t rows_pipe_smem(const DevPlan& p) {
+  return (static_cast<size_t>(rows_pipe_stage0(p)) + 2 * static_cast<size_t>(p.x_pitch) + p.nc) * sizeof(float2);
+}
 size_t sample_fwd_smem(const DevPlan& p) {
   return static_cast<size_t>(kSampleWarps) * p.r * (2 * sizeof(float4) + sizeof(float2) + sizeof(int2));
+}
+size_t scatter_fwd_smem(const DevPlan& p) {
+  return sample_fwd_smem(p) + kScatterBox * sizeof(float) + 4 * sizeof(int);
 }
 size_t cols_smem(const DevPlan& p) { return (2 * static_cast<size_t>(p.col_group) + 1) * p.n_theta * sizeof(float2); }
 size_t cols_t_smem(const DevPlan& p, int G) { return (2 * static_cast<size_t>(G) + 1) * p.n_theta * sizeof(float2); }
 
 template <bool BACK>
 void launch_rows_forward(const DevPlan& p, cudaStream_t st, int batch) {
+  if (!BACK && p.rows_pipe_fwd > 0) {
+    const int n_rows = p.M * p.nh * batch;
+    const int blocks = n_rows < p.rows_pipe_fwd ? n_rows : p.rows_pipe_fwd;
+    switch (p.row_fixed) {
+#define RADON_LAUNCH_ROWS_FWD_PIPE(i, ...) \
+  case i: k_rows_fwd_pipe<i><<<blocks, kThreads, rows_pipe_smem(p), st>>>(p, n_rows); break;
+      RADON_ROW_SEQUENCES(RADON_LAUNCH_ROWS_FWD_PIPE)
+#undef RADON_LAUNCH_ROWS_FWD_PIPE
+      default: k_rows_fwd_pipe<-1><<<blocks, kThreads, rows_pipe_smem(p), st>>>(p, n_rows); break;
+    }
+    return;
+  }
   const dim3 grid(p.nh, p.M, batch);
   // the back-projection rows keep the generic transform: with the compiled one its sampling
   // part ran slower (measured 78 -> 92 us at N = 2048)
@@ -1297,6 +1558,19 @@ void launch_columns_and_inverse(const DevPlan& p, const float2* kern, cudaStream
     k_columns<<<dim3(ngroups, p.M, batch), kThreads, cols_smem(p), st>>>(p, kern);
   }
   hook(stage0, st);
+  if (p.rows_pipe_inv > 0) {
+    const int n_rows = p.M * (p.nh + kHaloLo + kHaloHi) * batch;
+    const int blocks = n_rows < p.rows_pipe_inv ? n_rows : p.rows_pipe_inv;
+    switch (p.row_fixed) {
+#define RADON_LAUNCH_ROWS_INV_PIPE(i, ...) \
+  case i: k_rows_inv_pipe<i><<<blocks, kThreads, rows_pipe_smem(p), st>>>(p, n_rows); break;
+      RADON_ROW_SEQUENCES(RADON_LAUNCH_ROWS_INV_PIPE)
+#undef RADON_LAUNCH_ROWS_INV_PIPE
+      default: k_rows_inv_pipe<-1><<<blocks, kThreads, rows_pipe_smem(p), st>>>(p, n_rows); break;
+    }
+    hook(stage0 + 1, st);
+    return;
+  }
   const dim3 grid(p.nh + kHaloLo + kHaloHi, p.M, batch);
   switch (p.row_fixed) {
 #define RADON_LAUNCH_ROWS_INV(i, ...) \
@@ -1310,6 +1584,18 @@ void launch_columns_and_inverse(const DevPlan& p, const float2* kern, cudaStream
 
 }  // namespace
 
+// Raise the dynamic shared memory limit of a persistent forward / inverse row kernel pair to the
+// device maximum `optin` (the limit is per function, shared by every plan, so it is never set
+// lower) and report how many CTAs of each fit on one SM with `smem` bytes.
+template <class KF, class KI>
+cudaError_t configure_rows_pipe(KF* kf, KI* ki, int optin, size_t smem, int* per_sm_fwd, int* per_sm_inv) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_fwd, kf, kThreads, smem)) != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_inv, ki, kThreads, smem);
+}
+
 cudaError_t configure_kernels(DevPlan& p) {
   // The limit is a per-function attribute shared by every plan on the device: raise it to the
   // device's opt-in maximum (never to one plan's need, which a later, smaller plan would lower).
@@ -1321,7 +1607,7 @@ cudaError_t configure_kernels(DevPlan& p) {
   if (rows_smem(p) > static_cast<size_t>(optin)) p.rows_tw_smem = 0;
   p.filt_tw_smem = 1;
   if (filt_smem(p) > static_cast<size_t>(optin)) p.filt_tw_smem = 0;
-  if (sample_fwd_smem(p) > static_cast<size_t>(optin) || rows_smem(p) > static_cast<size_t>(optin) ||
+  if (scatter_fwd_smem(p) > static_cast<size_t>(optin) || rows_smem(p) > static_cast<size_t>(optin) ||
       cols_smem(p) > static_cast<size_t>(optin) || filt_smem(p) > static_cast<size_t>(optin))
     return cudaErrorInvalidValue;
   if ((e = cudaFuncSetAttribute(k_sino_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess) return e;
@@ -1329,6 +1615,12 @@ cudaError_t configure_kernels(DevPlan& p) {
   if ((e = cudaFuncSetAttribute(k_rows_fwd<false, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_sample_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_sample_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
+#define RADON_CONFIGURE_SAMPLE(n)                                                                                 \
+  if ((e = cudaFuncSetAttribute(k_sample_fwd<true, n + 2 * kPad>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != \
+      cudaSuccess)                                                                                                \
+    return e;
+  RADON_SAMPLE_PITCHES(RADON_CONFIGURE_SAMPLE)
+#undef RADON_CONFIGURE_SAMPLE
   if ((e = cudaFuncSetAttribute(k_rows_fwd<true, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_rows_inv<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)) != cudaSuccess) return e;
 #define RADON_CONFIGURE_ROWS(i, ...)                                                                                   \
@@ -1361,6 +1653,25 @@ cudaError_t configure_kernels(DevPlan& p) {
 #undef RADON_CONFIGURE_COLUMN
     if (e != cudaSuccess) return e;
   }
+  // persistent rho transforms: one CTA per resident slot, when their buffers fit
+  p.rows_pipe_fwd = p.rows_pipe_inv = 0;
+  const size_t ps = rows_pipe_smem(p);
+  if (ps <= static_cast<size_t>(optin)) {
+    int n_sm = 0, per_sm_fwd = 0, per_sm_inv = 0;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    switch (p.row_fixed) {
+#define RADON_CONFIGURE_ROWS_PIPE(i, ...)                                                                   \
+  case i:                                                                                                   \
+    e = configure_rows_pipe(k_rows_fwd_pipe<i>, k_rows_inv_pipe<i>, optin, ps, &per_sm_fwd, &per_sm_inv);          \
+    break;
+      RADON_ROW_SEQUENCES(RADON_CONFIGURE_ROWS_PIPE)
+#undef RADON_CONFIGURE_ROWS_PIPE
+      default: e = configure_rows_pipe(k_rows_fwd_pipe<-1>, k_rows_inv_pipe<-1>, optin, ps, &per_sm_fwd, &per_sm_inv);
+    }
+    if (e != cudaSuccess) return e;
+    p.rows_pipe_fwd = per_sm_fwd * n_sm;
+    p.rows_pipe_inv = per_sm_inv * n_sm;
+  }
   return cudaSuccess;
 }
 
@@ -1377,10 +1688,20 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
                                       kThreads, 0, st>>>(p, isrc, p.N, p.N, p.coef_img, p.img_pitch, kPad, p.bs_img);
   hook(0, st);
   const dim3 sgrid((p.n_eanc + 1) / 2, (p.nh + kSampleWarps - 1) / kSampleWarps, p.M * batch);
-  if (p.img_quad && p.interp == 3)
-    k_sample_fwd<true><<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
-  else
+  if (p.img_quad && p.interp == 3) {
+    switch (p.img_pitch) {
+#define RADON_LAUNCH_SAMPLE(n)                                                                    \
+  case n + 2 * kPad:                                                                              \
+    k_sample_fwd<true, n + 2 * kPad><<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);     \
+    break;
+      RADON_SAMPLE_PITCHES(RADON_LAUNCH_SAMPLE)
+#undef RADON_LAUNCH_SAMPLE
+      default:
+        k_sample_fwd<true><<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
+    }
+  } else {
     k_sample_fwd<false><<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
+  }
   hook(11, st);
   launch_rows_forward<false>(p, st, batch);
   hook(1, st);
@@ -1432,7 +1753,7 @@ cudaError_t launch_transpose(const DevPlan& p, const float* sino, float* image, 
   k_rows_c2r_t<<<dim3(p.nh, p.M, batch), kThreads, rows_smem(p), st>>>(p);
   hook(15, st);
   const dim3 sgrid((p.n_eanc + 1) / 2, (p.nh + kSampleWarps - 1) / kSampleWarps, p.M * batch);
-  k_scatter_fwd<<<sgrid, kSampleWarps * 32, sample_fwd_smem(p), st>>>(p);
+  k_scatter_fwd<<<sgrid, kSampleWarps * 32, scatter_fwd_smem(p), st>>>(p);
   hook(16, st);
   const CoefSource csrc{p.coef_img, p.N, p.img_pitch, p.bs_img};
   k_prefilter<CoefSource, false><<<dim3((p.N + kPfCols - 1) / kPfCols, (p.N + kPfRows - 1) / kPfRows, batch),

@@ -53,6 +53,8 @@ struct DevPlan {
   cudaTextureObject_t tex_lp;    // log-polar coefficients, M (nh + 4) rows x y_pitch columns
   cudaSurfaceObject_t surf_lp;   // write view (filled by the inverse rho FFT)
   int rows_tw_smem;    // 1: row kernels stage the rho twiddles in shared memory
+  int rows_pipe_fwd;   // > 0: resident CTAs of the persistent forward rho transform (0: one CTA per row)
+  int rows_pipe_inv;   // > 0: resident CTAs of the persistent inverse rho transform
   int row_fixed;       // kRowRadices index of the compiled row transform, -1: generic
   float* coef_sino;    // n_angles x sino_pitch, zero border
   float2* xspec;       // M x nh x x_pitch
