@@ -3,8 +3,12 @@
 Slices are grouped by size.  Each group runs as same-size batches of at most the plan's batch
 capacity (one set of launches per transform and batch: radon_forward_batch /
 radon_backproject_batch), and the whole multi-size sequence can be captured once in a CUDA graph
-and replayed.  `tune()` picks, per plan, the slices per batched call and the theta-convolution
-kernel by timing; neither changes results beyond FP32 rounding.
+and replayed.  `tune()` picks, per size, the slices per batched call and the theta-convolution
+kernel by timing (neither changes results beyond FP32 rounding) and, when several partition
+counts M are offered, the fastest M.  M sets the log-polar lattice (Section 2: beta = pi / M, the
+radial factor a_R, N_rho, n_theta), so a different M gives a different discretisation of the same
+transforms, each as accurate as the method (the tests compare every M against the oracle at that
+M); at M = 4 the angular FFT length is a power of two for N = n_angles in 256 ... 4096.
 """
 
 from __future__ import annotations
@@ -18,26 +22,36 @@ from . import binding
 
 class UnevenBatch:
     def __init__(self, sizes, n_angles_of=lambda n: n, n_det_of=lambda n: 3 * n // 2, interp_order: int = 3,
-                 n_partitions: int = 3, max_batch: int = 16):
+                 n_partitions=3, max_batch: int = 16):
+        """``n_partitions``: M for every size, or a sequence of candidate M values from which
+        ``tune()`` picks per size (the first one is used until then)."""
         self.sizes = [int(n) for n in sizes]
         self.groups = collections.OrderedDict()  # N -> list of slice indices
         for i, n in enumerate(self.sizes):
             self.groups.setdefault(n, []).append(i)
+        self.partition_candidates = tuple(n_partitions) if hasattr(n_partitions, "__iter__") else (int(n_partitions),)
+        self._geom = (n_angles_of, n_det_of, interp_order, max_batch)
         self.plans, self.images, self.sinos, self.chunk = {}, {}, {}, {}
         for n, idx in self.groups.items():
-            plan = binding.radon_plan_create(n, n_angles_of(n), n_det_of(n), interp_order, n_partitions)
-            cap = min(len(idx), max_batch)
-            while cap > 1:
-                try:
-                    binding.radon_plan_reserve_batch(plan, cap)
-                    break
-                except binding.RadonError:
-                    cap //= 2
+            plan = self._make_plan(n, self.partition_candidates[0])
             self.plans[n] = plan
-            self.chunk[n] = cap
             self.images[n] = torch.zeros((len(idx),) + plan.image_shape, device="cuda")
             self.sinos[n] = torch.zeros((len(idx),) + plan.sino_shape, device="cuda")
         self.graph = None
+
+    def _make_plan(self, n, M):
+        """Plan for size n with M partitions, batch capacity reserved (halved until it fits)."""
+        n_angles_of, n_det_of, interp_order, max_batch = self._geom
+        plan = binding.radon_plan_create(n, n_angles_of(n), n_det_of(n), interp_order, M)
+        cap = min(len(self.groups[n]), max_batch)
+        while cap > 1:
+            try:
+                binding.radon_plan_reserve_batch(plan, cap)
+                break
+            except binding.RadonError:
+                cap //= 2
+        self.chunk[n] = cap
+        return plan
 
     # ---------------------------------------------------------------- data in / out
     def set_images(self, images):
@@ -107,30 +121,46 @@ class UnevenBatch:
             binding.radon_backproject_batch(plan, self.sinos[n][s:s + c], self.images[n][s:s + c])
 
     def tune(self, groups=(0, 1, 2, 4), chunks=(1, 2, 4, 8, 16), repeats: int = 2):
-        """Per size group, choose the slices per batched call (up to the reserved capacity), then
-        the theta-convolution kernel, by timing R then R# over the whole group.  Neither choice
-        changes results beyond FP32 rounding of the theta kernel (chunking changes nothing).
-        Uses (and overwrites) the group buffers: set the inputs afterwards.  Returns
-        {N: (chunk, column group)}."""
+        """Per size group and candidate M, choose the slices per batched call (up to the reserved
+        capacity), then the theta-convolution kernel, by timing R then R# over the whole group;
+        then keep the fastest M.  Chunking changes nothing and the theta kernel only FP32
+        rounding; M changes the discretisation (see the module docstring).  Uses (and
+        overwrites) the group buffers: set the inputs afterwards, and capture after tuning.
+        Returns {N: (chunk, column group, M)}."""
         choice = {}
-        for n, plan in self.plans.items():
-            cap = self.chunk[n]
-            best = None
-            for c in sorted({min(c, cap) for c in chunks}):
-                self.chunk[n] = c
-                t = self._time_group(n, repeats)
-                if best is None or t < best[0]:
-                    best = (t, c)
-            self.chunk[n] = best[1]
-            best = None
-            for g in groups:
-                try:
-                    binding.radon_plan_set_column_group(plan, g)
-                except binding.RadonError:
-                    continue
-                t = self._time_group(n, repeats)
-                if best is None or t < best[0]:
-                    best = (t, g)
-            binding.radon_plan_set_column_group(plan, best[1])
-            choice[n] = (self.chunk[n], best[1])
+        for n in self.plans:
+            best_m = None
+            for M in self.partition_candidates:
+                plan = self.plans[n] if self.plans[n].info["n_partitions"] == M else self._make_plan(n, M)
+                self.plans[n] = plan
+                chunk, group, t = self._tune_plan(n, plan, groups, chunks, repeats)
+                if best_m is None or t < best_m[0]:
+                    best_m = (t, plan, chunk, group, M)
+            _, plan, chunk, group, M = best_m
+            self.plans[n] = plan
+            self.chunk[n] = chunk
+            binding.radon_plan_set_column_group(plan, group)
+            choice[n] = (chunk, group, M)
+        self.graph = None
         return choice
+
+    def _tune_plan(self, n, plan, groups, chunks, repeats):
+        cap = plan.max_batch if plan.max_batch > 1 else 1
+        best = None
+        for c in sorted({min(c, cap) for c in chunks}):
+            self.chunk[n] = c
+            t = self._time_group(n, repeats)
+            if best is None or t < best[0]:
+                best = (t, c)
+        self.chunk[n] = best[1]
+        best_g = None
+        for g in groups:
+            try:
+                binding.radon_plan_set_column_group(plan, g)
+            except binding.RadonError:
+                continue
+            t = self._time_group(n, repeats)
+            if best_g is None or t < best_g[0]:
+                best_g = (t, g)
+        binding.radon_plan_set_column_group(plan, best_g[1])
+        return self.chunk[n], best_g[1], best_g[0]

@@ -104,7 +104,7 @@ def test_uneven_batch_with_graph_matches_per_slice(rl):
     ub = UnevenBatch(sizes, max_batch=2)
     choice = ub.tune()
     assert set(choice) == {64, 96, 128}
-    assert all(1 <= c <= 2 and g in (0, 1, 2, 4) for c, g in choice.values())
+    assert all(1 <= c <= 2 and g in (0, 1, 2, 4) and M == 3 for c, g, M in choice.values())
     imgs = [_t(ellipse_image(n, random_ellipses(6, 40 + i))) for i, n in enumerate(sizes)]
     ub.set_images(imgs)
     ub.forward()
@@ -120,3 +120,30 @@ def test_uneven_batch_with_graph_matches_per_slice(rl):
     torch.cuda.synchronize()
     for i in range(len(sizes)):
         assert torch.equal(ub.sinogram(i), eager[i])
+
+
+def test_uneven_batch_tunes_the_partition_count_and_matches_the_oracle(rl):
+    """With candidate partition counts the tuner keeps the fastest M per size; every slice then
+    matches the FP64 log-polar oracle at that M (Algorithms 1 and 2 with beta = pi / M)."""
+    from oracle import geometry, logpolar
+    from paper_1506_00014_gb300.batch import UnevenBatch
+
+    sizes = [64, 96, 64, 128]
+    ub = UnevenBatch(sizes, n_partitions=(3, 4), max_batch=2)
+    choice = ub.tune()
+    assert set(choice) == {64, 96, 128} and all(M in (3, 4) for _, _, M in choice.values())
+    imgs = [_t(ellipse_image(n, random_ellipses(6, 50 + i))) for i, n in enumerate(sizes)]
+    ub.capture()  # runs R then R# once before capturing: the inputs are set afterwards
+    ub.set_images(imgs)
+    ub.replay()
+    torch.cuda.synchronize()
+    for i, n in enumerate(sizes):
+        M = choice[n][2]
+        assert ub.plans[n].info["n_partitions"] == M
+        geo = geometry.make_geometry(n, n, 3 * n // 2, M, 3)
+        ref_s = logpolar.forward(imgs[i].cpu().numpy().astype(np.float64), geo)
+        got_s = ub.sinogram(i).cpu().numpy()
+        assert np.linalg.norm(got_s - ref_s) / np.linalg.norm(ref_s) < 1e-5
+        ref_b = logpolar.backproject(got_s.astype(np.float64), geo)
+        got_b = ub.image(i).cpu().numpy()
+        assert np.linalg.norm(got_b - ref_b) / np.linalg.norm(ref_b) < 1e-5
