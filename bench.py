@@ -140,6 +140,28 @@ def stage_bytes(info):
     }
 
 
+def live_bin_count(n_det: int) -> int:
+    """Detector bins with |s| < 1 (exact integer test 2 (2k - n_det)^2 < n_det^2)."""
+    return sum(1 for k in range(n_det) if 2 * (2 * k - n_det) ** 2 < n_det * n_det)
+
+
+def pair_bytes(info) -> dict:
+    """Algorithmic bytes of one R and one R# with the log-polar convolution fused:
+    B_R  = 4 N^2 + 4 n_angles n_det + 4 S_c + |K|
+    B_R# = 4 n_angles n_live + 4 N^2 + 4 S_c + |K|
+    where S_c = M n_theta_half (N_rho/2 + 1) 8 is the half spectrum of the kept theta rows (written
+    and read twice per transform: between the rho pass and the theta pass, and between the theta
+    pass and the inverse rho pass), |K| = (n_theta/2 + 1)(N_rho/2 + 1) 8 the kernel table read once,
+    and n_live the detector bins with |s| < 1 (the only ones R# reads)."""
+    n, na, nd, mm = info["N"], info["n_angles"], info["n_det"], info["n_partitions"]
+    nh, nr, nt = info["n_theta_half"], info["N_rho"], info["n_theta"]
+    S_c = mm * nh * (nr // 2 + 1) * 8
+    K = (nt // 2 + 1) * (nr // 2 + 1) * 8
+    B_R = 4 * n * n + 4 * na * nd + 4 * S_c + K
+    B_B = 4 * na * live_bin_count(nd) + 4 * n * n + 4 * S_c + K
+    return {"R": B_R, "R#": B_B, "pair": B_R + B_B, "S_c": S_c, "K": K}
+
+
 def _event_ms(torch, fn, reps: int, flush=None) -> float:
     """Median CUDA-event time of fn() over reps runs on the current stream (L2 flushed before each)."""
     import statistics
@@ -157,7 +179,65 @@ def _event_ms(torch, fn, reps: int, flush=None) -> float:
     return statistics.median(times)
 
 
-def bench_batched(rl, torch, flush) -> dict:
+def closed_form_errors(rl, torch, plan) -> dict:
+    """R of sampled Gaussians against their analytic Radon transform and R# of that analytic
+    sinogram against its closed-form back-projection, through ``plan`` (sizes the oracle cannot
+    finish in seconds)."""
+    import numpy as np
+
+    from oracle import direct, geometry
+    from workloads import gaussian_image
+
+    info = plan.info
+    n, na, nd = info["N"], info["n_angles"], info["n_det"]
+    geo = geometry.make_geometry(n, na, nd, info["n_partitions"], info["interp_order"])
+    blobs = [(0.2, -0.1, 0.12, 1.0), (-0.3, 0.25, 0.08, -0.7), (0.05, 0.5, 0.1, 0.4)]
+    th = np.arange(na) * geo.dtheta
+    s = (np.arange(nd) - nd / 2) * geo.ds
+    sino = direct.gaussian_radon(th[:, None], s[None, :], blobs)
+    sino[:, ~geometry.live_bins(nd)] = 0.0
+    x = (np.arange(n) - n / 2) * (2.0 / n)
+    bp = np.zeros((n, n))
+    for cx, cy, sg, w in blobs:
+        bp += w * math.sqrt(2 * math.pi) * sg * direct.gaussian_bp(np.hypot(x[None, :] - cx, x[:, None] - cy), sg)
+    bp[~geometry.disc_mask(n)] = 0.0
+    f = torch.from_numpy(gaussian_image(n, blobs).astype(np.float32)).cuda()
+    g = torch.from_numpy(sino.astype(np.float32)).cuda()
+    Rf = torch.empty((na, nd), device="cuda")
+    Bg = torch.empty((n, n), device="cuda")
+    rl.radon_forward(plan, f, Rf)
+    rl.radon_backproject(plan, g, Bg)
+    torch.cuda.synchronize()
+    return {"R": rel_l2(Rf.cpu().numpy(), sino), "R#": rel_l2(Bg.cpu().numpy(), bp),
+            "reference": "closed forms: analytic Radon transform of 3 Gaussians and its back-projection "
+                         "pi sqrt(2 pi) s e^-u I0(u)", "metric": "relative L2"}
+
+
+def oracle_errors(rl, torch, plan, seed: int = 11) -> dict:
+    """R of a seeded smooth image and R# of a seeded N(0, 1) sinogram through ``plan`` against the
+    FP64 log-polar oracle on the same FP32 inputs (whole outputs)."""
+    import numpy as np
+
+    from oracle import geometry, logpolar
+    from workloads import random_sinogram, smooth_random_image
+
+    info = plan.info
+    n, na, nd = info["N"], info["n_angles"], info["n_det"]
+    geo = geometry.make_geometry(n, na, nd, info["n_partitions"], info["interp_order"])
+    f = smooth_random_image(n, seed).astype(np.float32)
+    g = random_sinogram(na, nd, seed + 1).astype(np.float32)
+    Rf = torch.empty((na, nd), device="cuda")
+    Bg = torch.empty((n, n), device="cuda")
+    rl.radon_forward(plan, torch.from_numpy(f).cuda(), Rf)
+    rl.radon_backproject(plan, torch.from_numpy(g).cuda(), Bg)
+    torch.cuda.synchronize()
+    return {"R": rel_l2(Rf.cpu().numpy(), logpolar.forward(f.astype(np.float64), geo)),
+            "R#": rel_l2(Bg.cpu().numpy(), logpolar.backproject(g.astype(np.float64), geo)),
+            "tolerance": 1e-5, "metric": "relative L2",
+            "inputs": f"smooth random image (seed {seed}), N(0,1) sinogram (seed {seed + 1}), this plan's geometry"}
+
+
+def bench_batched(rl, torch, flush, with_oracle: bool = True) -> dict:
     """96 slices of uneven N drawn from {256, 512, 1024, 2048, 4096} (seed 4), n_angles = N,
     n_det = 1.5 N: per-slice calls versus same-size batches replayed from one CUDA graph.  One
     pass = R of every image, then R# of every sinogram.  Inputs are seeded uniform images; the
@@ -166,7 +246,7 @@ def bench_batched(rl, torch, flush) -> dict:
     from workloads import slice_sizes
 
     sizes = slice_sizes(96, 4)
-    ub = UnevenBatch(sizes, max_batch=16)
+    ub = UnevenBatch(sizes, max_batch=16, n_partitions=(3, 4))
     gen = torch.Generator(device="cuda")
     for i, n in enumerate(sizes):
         gen.manual_seed(100 + i)
@@ -184,22 +264,60 @@ def bench_batched(rl, torch, flush) -> dict:
 
     per_slice()
     t_slice = _event_ms(torch, per_slice, 3, flush)
-    choice = ub.tune()  # slices per batched call and theta kernel, per size group
+    choice = ub.tune()  # slices per batched call, theta kernel and partition count, per size group
+    per_slice()
+    t_slice_tuned = _event_ms(torch, per_slice, 3, flush)  # per-slice calls of the tuned plans
     ub.capture()
     ub.replay()
     t_graph = _event_ms(torch, ub.replay, 3, flush)
     samples = sum(n * n + n * (3 * n // 2) for n in sizes)
+
+    # accuracy: fresh seeded inputs and one replay; the first slice of each size is compared with
+    # per-slice calls of its plan (bit for bit) and with the FP64 oracle
+    import numpy as np
+
+    from oracle import geometry, logpolar
+
+    for i, n in enumerate(sizes):
+        gen.manual_seed(100 + i)
+        ub.image(i).copy_(torch.rand((n, n), device="cuda", generator=gen))
+    firsts = {n: idx[0] for n, idx in ub.groups.items()}
+    f0 = {n: ub.image(i).clone() for n, i in firsts.items()}
+    ub.replay()
+    torch.cuda.synchronize()
+    accuracy = {}
+    for n, i in firsts.items():
+        plan = ub.plans[n]
+        s1 = torch.empty(plan.sino_shape, device="cuda")
+        b1 = torch.empty(plan.image_shape, device="cuda")
+        rl.radon_forward(plan, f0[n], s1)
+        rl.radon_backproject(plan, ub.sinogram(i), b1)
+        torch.cuda.synchronize()
+        entry = {"slice": i, "batched_equals_per_slice": bool(torch.equal(s1, ub.sinogram(i)) and
+                                                              torch.equal(b1, ub.image(i)))}
+        if with_oracle and n <= 1024:
+            geo = geometry.make_geometry(n, n, 3 * n // 2, plan.info["n_partitions"], 3)
+            ref_s = logpolar.forward(f0[n].cpu().numpy().astype(np.float64), geo)
+            ref_b = logpolar.backproject(ub.sinogram(i).cpu().numpy().astype(np.float64), geo)
+            entry["err_vs_oracle"] = {"R": rel_l2(ub.sinogram(i).cpu().numpy(), ref_s),
+                                      "R#": rel_l2(ub.image(i).cpu().numpy(), ref_b), "tolerance": 1e-5,
+                                      "oracle": "FP64 log-polar oracle, this slice's inputs", "metric": "relative L2"}
+        elif with_oracle:
+            entry["err_vs_closed_form"] = closed_form_errors(rl, torch, plan)
+        accuracy[str(n)] = entry
     return {
         "slices": len(sizes), "sizes": {str(n): len(v) for n, v in ub.groups.items()},
-        "per_slice_ms": t_slice, "batched_graph_ms": t_graph, "speedup": t_slice / t_graph,
-        "tuned": {str(n): {"slices_per_call": c, "column_group": g} for n, (c, g) in choice.items()},
+        "per_slice_ms": t_slice, "per_slice_tuned_plans_ms": t_slice_tuned, "batched_graph_ms": t_graph,
+        "speedup": t_slice / t_graph,
+        "baseline": "per_slice_ms: one call per slice and transform, M = 3, default theta kernel",
+        "tuned": {str(n): {"slices_per_call": c, "column_group": g, "n_partitions": m}
+                  for n, (c, g, m) in choice.items()},
         "batched_samples_per_s": samples / (t_graph / 1e3), "unit": UNIT,
-        "results": "batched calls equal per-slice calls bit for bit (tests/test_gpu_batch.py); the tuned "
-                   "theta kernel may differ from the default by FP32 rounding",
+        "accuracy": accuracy,
     }
 
 
-def bench_least_squares(rl, torch) -> dict:
+def bench_least_squares(rl, torch, with_oracle: bool = True) -> dict:
     """64 slices, N = 1024, 720 angles, 1536 bins; data = analytic ellipse line integrals plus
     Gaussian noise at 1 % of the maximum (seeds 200 + i); 50 gradient steps of ||R f - g||^2:
     the per-slice eager loop versus the batched autograd loop (backward = R#) replayed from a CUDA
@@ -242,28 +360,78 @@ def bench_least_squares(rl, torch) -> dict:
     ref = torch.stack(ref)
     diff = float((got - ref).norm() / ref.norm())
     loss0 = float((g * g).sum())
-    return {
+    out = {
         "slices": slices, "N": n, "n_angles": na, "n_det": nd, "steps": steps,
         "per_slice_eager_ms": t_slice, "batched_autograd_graph_ms": t_batch, "speedup": t_slice / t_batch,
         "rel_diff_batched_vs_per_slice": diff, "loss_ratio_final_over_initial": float(bl.losses().sum()) / loss0,
     }
+    if with_oracle:
+        out["err_vs_oracle"] = oracle_errors(rl, torch, plan)
+    return out
 
 
-def bench_fbp_large(rl, torch, flush) -> dict:
-    """FBP at N = 8192 with 8192 angles and 12288 bins, Shepp-Logan window, then R#: one call of
-    radon_fbp on a seeded N(0, 1) sinogram (the work does not depend on the values)."""
+def bench_fbp_large(rl, torch, flush, with_oracle: bool = True) -> dict:
+    """FBP at N = 8192 with 8192 angles x 12288 bins, Shepp-Logan window, then R#.  The sinogram is
+    the analytic line integrals of 200 random ellipses (seed 5) plus Gaussian noise with sigma =
+    0.5 % of its maximum (seed 5).  Accuracy: against the phantom itself (closed form: 4 x 4
+    sub-pixel coverage at 4096 seeded pixels of the disc), and against the direct oracle (the FP64
+    filter of the same noisy sinogram, then the rectangle rule over the 8192 angles with cubic
+    interpolation in s) at 256 of those pixels."""
+    import numpy as np
+
+    from workloads import ellipse_sinogram_torch, ellipse_values_at, random_ellipses
+
     n, na, nd = 8192, 8192, 12288
+    ell = random_ellipses(200, 5)
+    g64 = ellipse_sinogram_torch(ell, na, nd, "cuda")
+    sigma = 0.005 * float(g64.abs().max())
+    noise = torch.from_numpy(np.random.default_rng(5).standard_normal((na, nd), dtype=np.float32)).cuda()
+    g = (g64 + sigma * noise.double()).float()
+    g_clean = g64.float()
+    del g64, noise
     plan = rl.radon_plan_create(n, na, nd, 3, 3)
-    gen = torch.Generator(device="cuda").manual_seed(5)
-    g = torch.randn((na, nd), device="cuda", generator=gen)
     img = torch.empty((n, n), device="cuda")
     fn = lambda: rl.radon_fbp(plan, g, img, rl.RADON_FILTER_SHEPP_LOGAN)  # noqa: E731
     for _ in range(2):
         fn()
     t = _event_ms(torch, fn, 5, flush)
-    return {"N": n, "n_angles": na, "n_det": nd, "filter": "shepp-logan", "ms_per_fbp": t,
-            "output_pixels_per_s": n * n / (t / 1e3),
-            "accuracy": "closed form (FBP of analytic Gaussians) checked in tests/test_gpu_parity.py"}
+    fn()
+    torch.cuda.synchronize()
+    out = {"N": n, "n_angles": na, "n_det": nd, "filter": "shepp-logan", "ms_per_fbp": t,
+           "output_pixels_per_s": n * n / (t / 1e3),
+           "data": "analytic sinogram of 200 random ellipses (seed 5) + N(0, (0.005 max)^2) noise (seed 5)"}
+    rng = np.random.default_rng(6)
+    v = 2 * np.arange(n) - n
+    ii, jj = np.nonzero((v[:, None] ** 2 + v[None, :] ** 2) < n * n)
+    sel = rng.choice(ii.size, 4096, replace=False)
+    rows, cols = ii[sel], jj[sel]
+    got = img.cpu().numpy()[rows, cols].astype(np.float64)
+    truth = ellipse_values_at(ell, n, rows, cols)
+    rl.radon_fbp(plan, g_clean, img, rl.RADON_FILTER_SHEPP_LOGAN)
+    torch.cuda.synchronize()
+    got_clean = img.cpu().numpy()[rows, cols].astype(np.float64)
+    out["err_vs_phantom"] = {
+        "noisy": rel_l2(got, truth), "noise_free": rel_l2(got_clean, truth), "metric": "relative L2",
+        "sample": "4096 disc pixels (seed 6)",
+        "note": "reconstruction error against the phantom itself: the noisy figure is dominated by the 0.5 % noise "
+                "that the ramp amplifies; the noise-free one (same FBP of the analytic sinogram) by the ellipse edges"}
+    if with_oracle:
+        from oracle import direct, fbp, geometry
+
+        geo = geometry.make_geometry(n, na, nd, 3, 3)
+        k = 256
+        out["err_vs_direct_sampled"] = {"metric": "relative L2", "sample": f"{k} of the pixels above",
+                                        "oracle": "FP64 Shepp-Logan filter of the same sinogram, then the rectangle "
+                                                  "rule over the angles (a different discretisation of R#)"}
+        for name, sino, vals in (("noise_free", g_clean, got_clean), ("noisy", g, got)):
+            gh = sino.cpu().numpy().astype(np.float64)
+            Wg = np.empty_like(gh)
+            for a0 in range(0, na, 512):
+                Wg[a0:a0 + 512] = fbp.filter_sinogram(gh[a0:a0 + 512], geo, "shepp-logan")
+            ref = direct.backproject_direct(Wg, geo, pixels=(rows[:k], cols[:k]))
+            out["err_vs_direct_sampled"][name] = rel_l2(vals[:k], ref)
+    del plan
+    return out
 
 
 def bench_exact_transpose(rl, torch, flush) -> dict:
@@ -290,12 +458,19 @@ def bench_exact_transpose(rl, torch, flush) -> dict:
     stages = rl.radon_profile_read(plan)
     rl.radon_profile_enable(plan, False)
     out["stage_ms_R^T"] = {k: round(ms / n, 4) for k, (ms, n) in stages.items() if n}
-    out["accuracy"] = ("parity with the oracle's transpose of Algorithm 1 and the dot-product identity, "
-                       "tests/test_gpu_transpose.py")
+    calls["R"]()
+    calls["R^T"]()
+    torch.cuda.synchronize()
+    lhs = float((sino.double() * g.double()).sum())
+    rhs = float((f.double() * img.double()).sum())
+    out["dot_product_identity"] = {
+        "abs_diff_over_norms": abs(lhs - rhs) / float(sino.double().norm() * g.double().norm()),
+        "identity": "<R f, g> = <f, R^T g> (plain sums), this workload; parity with the oracle's transpose is "
+                    "tested at smaller sizes"}
     return out
 
 
-def bench_em_volume(rl, torch, n: int = 256, iters: int = 100) -> dict:
+def bench_em_volume(rl, torch, n: int = 256, iters: int = 100, with_oracle: bool = True) -> dict:
     """100 EM iterations (Section 8) on an n x n x n volume: n slices, 1.5 n angles, n bins,
     M = 3 (the paper's EM timing setup), data = analytic line integrals of non-negative random
     ellipses (32 phantoms, seeds 300 + i, repeated over the slices); everything stays on the GPU
@@ -325,12 +500,15 @@ def bench_em_volume(rl, torch, n: int = 256, iters: int = 100) -> dict:
     for b0 in range(0, n, 64):
         rl.radon_forward_batch(plan, f[b0:b0 + 64].contiguous(), s[b0:b0 + 64])
     resid = float(torch.linalg.norm(s - g) / torch.linalg.norm(g))
-    return {"volume": f"{n}^3", "slices": n, "n_angles": na, "n_det": nd, "iterations": iters,
-            "seconds": t0.elapsed_time(t1) / 1e3, "relative_data_residual": resid,
-            "paper_gtx770_seconds": {"256": 88.0, "512": 690.0, "1024": 5400.0, "2048": 42000.0}.get(str(n))}
+    out = {"volume": f"{n}^3", "slices": n, "n_angles": na, "n_det": nd, "iterations": iters,
+           "seconds": t0.elapsed_time(t1) / 1e3, "relative_data_residual": resid,
+           "paper_gtx770_seconds": {"256": 88.0, "512": 690.0, "1024": 5400.0, "2048": 42000.0}.get(str(n))}
+    if with_oracle:
+        out["err_vs_oracle"] = oracle_errors(rl, torch, plan)
+    return out
 
 
-def bench_paper_table1(rl, torch, flush) -> dict:
+def bench_paper_table1(rl, torch, flush, with_oracle: bool = True) -> dict:
     """R# per slice on the paper's own back-projection workload (Table 1): N x N images from
     1.5 N angles x N bins, M = 3, slices batched (the paper batched slices to fill GPU memory);
     the forward R on the same shapes beside it (the paper reports R only inside the EM loop).
@@ -353,28 +531,49 @@ def bench_paper_table1(rl, torch, flush) -> dict:
         t_fwd = _event_ms(torch, fwd, 5, flush) / batch
         out[str(n)] = {"n_angles": na, "n_det": nd, "batch": batch, "ms_per_slice": t,
                        "paper_gtx770_ms_per_slice": 1e3 * paper[n], "forward_ms_per_slice": t_fwd}
+        if with_oracle:
+            out[str(n)]["err_vs_oracle" if n <= 1024 else "err_vs_closed_form"] = (
+                oracle_errors(rl, torch, plan) if n <= 1024 else closed_form_errors(rl, torch, plan))
         del plan, g, img
     return out
 
 
-def _ncu_summary() -> dict:
-    """Per stage (DRAM bytes per launch, L1/TEX %, issue %) from the committed ncu summary."""
-    out = {}
-    path = os.path.join(ROOT, "profiles", "dram_traffic_radon_pair_N2048.txt")
+KERNEL_SOURCES = ("radon_kernels.cu", "radon_kernels.cuh", "radon_fft.cuh")
+NCU_SUMMARY = os.path.join(ROOT, "profiles", "dram_traffic_radon_pair_N2048.txt")
+
+
+def kernel_sources_sha() -> str:
+    """sha256 (first 16 hex digits) over the CUDA sources of the transform kernels."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1506_00014_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_summary(path: str = NCU_SUMMARY) -> tuple[dict, str | None, str | None]:
+    """Per stage (DRAM bytes per launch, L1/TEX %, issue %, binding unit) from a committed ncu
+    summary, with the kernel-source hash and commit it was captured at.  The figures are returned
+    only while the kernels are unchanged since that capture (same source hash); else {}."""
+    out, sha, commit = {}, None, None
     try:
         with open(path) as fh:
             for line in fh:
-                parts = line.split()
-                if len(parts) == 4 and not line.startswith("#"):
-                    out[parts[0]] = tuple(float(x) for x in parts[1:])
+                if line.startswith("# kernel_sources_sha256:"):
+                    sha = line.split(":", 1)[1].strip()
+                elif line.startswith("# commit:"):
+                    commit = line.split(":", 1)[1].strip()
+                elif line.strip() and not line.startswith("#"):
+                    parts = line.split()
+                    if len(parts) == 5:
+                        out[parts[0]] = (float(parts[1]), float(parts[2]), float(parts[3]), parts[4])
     except OSError:
-        pass
-    return out
-
-
-def _dram_traffic() -> dict:
-    """Per-launch DRAM bytes by stage from the committed ncu summary (empty if absent)."""
-    return {k: v[0] for k, v in _ncu_summary().items()}
+        return {}, None, None
+    if sha is None or sha != kernel_sources_sha():
+        return {}, sha, commit
+    return out, sha, commit
 
 
 def reduce_max(value: float, dist, device) -> float:
@@ -498,8 +697,10 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = nbytes[dom] / (dom_ms / 1e3) / 1e9
     stage_ms = {k: round(v[0] / v[1], 4) for k, v in stage.items() if v[1]}  # stages the pair launched
-    traffic = _dram_traffic().get(dom)
-    summary = _ncu_summary().get(dom)
+    ncu, ncu_sha, ncu_commit = ncu_summary()
+    summary = ncu.get(dom)
+    traffic = summary[0] if summary else None
+    pb = pair_bytes(info)
 
     # the linear-interpolation variant of the same workload (same timing rules, fewer steps)
     plan_lin = rl.radon_plan_create(N, N_ANGLES, N_DET, 1, M)
@@ -518,6 +719,7 @@ def run_ours(args):
         ev_lin[k][1].record(stream)
     torch.cuda.synchronize()
     lin_ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev_lin), dist if world > 1 else None, dev) / n_lin
+    lin_out = (sino_d.cpu().numpy(), img_d.cpu().numpy())  # R f and R# g of the linear variant
     linear = {"interp_order": 1, "ms_per_step": lin_ms, "steps": n_lin,
               "value": whole_job_rate(world, _samples_per_step(), 1, lin_ms / 1e3), "unit": UNIT}
     del plan_lin
@@ -568,13 +770,14 @@ def run_ours(args):
 
     extras = {}
     if world == 1 and not args.no_extras:
-        extras["batched"] = bench_batched(rl, torch, flush)
-        extras["least_squares"] = bench_least_squares(rl, torch)
-        extras["fbp_8192"] = bench_fbp_large(rl, torch, flush)
+        extras["batched"] = bench_batched(rl, torch, flush, with_oracle=not args.no_cpu_baseline)
+        extras["least_squares"] = bench_least_squares(rl, torch, with_oracle=not args.no_cpu_baseline)
+        extras["fbp_8192"] = bench_fbp_large(rl, torch, flush, with_oracle=not args.no_cpu_baseline)
         extras["exact_transpose"] = bench_exact_transpose(rl, torch, flush)
-        extras["paper_table1_backprojection"] = bench_paper_table1(rl, torch, flush)
-        extras["em_volume_256"] = bench_em_volume(rl, torch, 256)
-        extras["em_volume_512"] = bench_em_volume(rl, torch, 512)
+        extras["paper_table1_backprojection"] = bench_paper_table1(rl, torch, flush,
+                                                                   with_oracle=not args.no_cpu_baseline)
+        extras["em_volume_256"] = bench_em_volume(rl, torch, 256, with_oracle=not args.no_cpu_baseline)
+        extras["em_volume_512"] = bench_em_volume(rl, torch, 512, with_oracle=not args.no_cpu_baseline)
 
     cpu = None
     err = None
@@ -587,6 +790,10 @@ def run_ours(args):
         err["vs_direct_sampled"] = err_vs_direct(
             _geometry.make_geometry(N, N_ANGLES, N_DET, M, INTERP), f, g,
             {"cuda": (h_s.numpy(), h_i.numpy()), "logpolar_oracle": (ref_s, ref_i)})
+        _, (lin_s, lin_i) = cpu_baseline(f, g, interp=1)
+        linear["err_vs_oracle"] = {"R": rel_l2(lin_out[0], lin_s), "R#": rel_l2(lin_out[1], lin_i), "tolerance": 1e-5,
+                                   "oracle": "FP64 log-polar oracle, linear interpolation, same inputs",
+                                   "metric": "relative L2"}
         err["vs_direct_sampled"]["note"] = (
             "the method's discretisation against exact line integrals (R, ellipse phantom) and the "
             "rectangle rule over angles (R#, white-noise sinogram: the two angular discretisations "
@@ -605,13 +812,24 @@ def run_ours(args):
                      "both on one stream",
         "serial_ms_per_step": serial_ms,
         "roofline": {
-            "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            # the dominant kernel's algorithmic bytes against the measured HBM copy bandwidth; its
+            # binding unit (from ncu) is L1/TEX or instruction issue, not DRAM
+            "bound": summary[3] if summary else "l1tex", "kernel": dom, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes": nbytes[dom], "ms_per_launch": dom_ms,
+            "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, captured at "
+                               f"commit {ncu_commit} (kernel sources {ncu_sha}, unchanged since)") if summary else
+                              f"null: the kernel sources ({kernel_sources_sha()}) changed since the last ncu capture",
             "binding_units_ncu": None if summary is None else {
                 "l1tex_pct_of_peak": summary[1], "issue_pct_of_peak": summary[2],
-                "note": "not HBM-bound: the kernel is limited by L1/TEX and instruction issue "
-                        "(profiles/kernels_radon_pair_N2048.md)"},
+                "note": "DRAM throughput is a few percent of peak; L1/TEX and issue bind this kernel"},
+            "pair": {
+                "bytes": pb["pair"], "bytes_R": pb["R"], "bytes_R#": pb["R#"],
+                "model": "B_R = 4N^2 + 4 n_angles n_det + 4 S_c + |K|, B_R# = 4 n_angles n_live + 4N^2 + 4 S_c + |K|, "
+                         f"S_c = M n_theta_half (N_rho/2+1) 8 = {pb['S_c']}, |K| = (n_theta/2+1)(N_rho/2+1) 8 = {pb['K']}",
+                "ms": ms_per_step, "achieved": pb["pair"] / (ms_per_step / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": pb["pair"] / (ms_per_step / 1e3) / 1e9 / peak,
+            },
         },
         "cpu_baseline": cpu,
         "err_vs_oracle": err,
@@ -626,7 +844,7 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(f, g, partitions=None):
+def cpu_baseline(f, g, partitions=None, interp=INTERP):
     """FP64 log-polar oracle on the host cores: R f and R# g of the same inputs, all partitions
     (partitions=None) or the listed ones; kernel tables and DFT matrices are set up outside the
     timed interval.  Returns (the cpu_baseline object, (R f, R# g))."""
@@ -634,7 +852,7 @@ def cpu_baseline(f, g, partitions=None):
 
     from oracle import geometry, kernels, logpolar
 
-    geo = geometry.make_geometry(N, N_ANGLES, N_DET, M, INTERP)
+    geo = geometry.make_geometry(N, N_ANGLES, N_DET, M, interp)
     KR = kernels.multiplier(geo, "R")
     KB = kernels.multiplier(geo, "B")
     dft = logpolar._Dft(geo)

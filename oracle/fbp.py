@@ -20,6 +20,7 @@ W filters each sinogram row along s, with bins |s| >= 1 taken as zero.
 
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -45,8 +46,10 @@ def ramp_kernel(P: int, ds: float) -> np.ndarray:
     return h
 
 
+@functools.lru_cache(maxsize=8)
 def transfer(P: int, ds: float, kind: str) -> np.ndarray:
-    """Transfer function on the full P-point DFT grid (real and even)."""
+    """Transfer function on the full P-point DFT grid (real and even).  Cached per (P, ds, kind);
+    callers must not modify the returned array."""
     h = ramp_kernel(P, ds)
     k = np.arange(P)
     # the DFT of the even real kernel, written out as a cosine sum
@@ -61,6 +64,7 @@ def transfer(P: int, ds: float, kind: str) -> np.ndarray:
         H = H * np.cos(x)
     elif kind != "ramp":
         raise ValueError(kind)
+    H.flags.writeable = False  # shared by the cache
     return H
 
 

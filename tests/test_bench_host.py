@@ -27,11 +27,34 @@ def test_byte_model_covers_the_transform_stages():
     assert all(v > 0 for v in model.values())
 
 
-def test_dram_traffic_summary_names_known_stages():
-    traffic = bench._dram_traffic()
-    assert traffic, "profiles/dram_traffic_radon_pair_N2048.txt is missing or empty"
-    assert set(traffic) <= set(binding.STAGE_NAMES)
-    assert all(v > 0 for v in traffic.values())
+def test_ncu_summary_is_used_only_for_the_kernels_it_was_captured_from(tmp_path):
+    rows = "sample_fwd 76370000 77.8 69.6 l1tex\ngather_sino 33660000 89.3 68.1 l1tex\n"
+    good = tmp_path / "good.txt"
+    good.write_text(f"# commit: abc1234\n# kernel_sources_sha256: {bench.kernel_sources_sha()}\n" + rows)
+    out, sha, commit = bench.ncu_summary(str(good))
+    assert commit == "abc1234" and sha == bench.kernel_sources_sha()
+    assert out["sample_fwd"] == (76370000.0, 77.8, 69.6, "l1tex")
+    assert set(out) <= set(binding.STAGE_NAMES)
+    stale = tmp_path / "stale.txt"
+    stale.write_text("# commit: abc1234\n# kernel_sources_sha256: 0000000000000000\n" + rows)
+    assert bench.ncu_summary(str(stale))[0] == {}
+    assert bench.ncu_summary(str(tmp_path / "missing.txt"))[0] == {}
+
+
+def test_committed_ncu_summary_parses():
+    out, sha, commit = bench.ncu_summary()
+    assert sha is not None and commit is not None
+    assert all(len(v) == 4 and v[0] > 0 for v in out.values())
+
+
+def test_pair_byte_model_at_the_single_slice_workload():
+    """B_R = 4N^2 + 4 n_angles n_det + 4 S_c + |K| ~ 198 MB and B_R# ~ 190 MB at N = 2048."""
+    from oracle import geometry
+
+    b = bench.pair_bytes(_info())
+    assert abs(b["R"] / 198.1e6 - 1) < 0.01 and abs(b["R#"] / 190.7e6 - 1) < 0.01
+    assert b["pair"] == b["R"] + b["R#"]
+    assert bench.live_bin_count(bench.N_DET) == int(geometry.live_bins(bench.N_DET).sum())
 
 
 def test_samples_per_step_counts_both_outputs():

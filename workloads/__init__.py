@@ -10,6 +10,8 @@ from .phantoms import (  # noqa: F401
     random_ellipses,
     ellipse_image,
     ellipse_sinogram,
+    ellipse_sinogram_torch,
+    ellipse_values_at,
     gaussian_image,
     random_sinogram,
     smooth_random_image,

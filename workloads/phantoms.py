@@ -122,6 +122,46 @@ def ellipse_sinogram(ellipses: list[Ellipse], n_angles: int, n_det: int) -> np.n
     return out
 
 
+def ellipse_sinogram_torch(ellipses: list[Ellipse], n_angles: int, n_det: int, device="cuda"):
+    """``ellipse_sinogram`` evaluated with torch in float64 on ``device`` (the same chord-length
+    formula; for sinograms too large to build quickly on the host)."""
+    import math
+
+    import torch
+
+    th = (torch.arange(n_angles, dtype=torch.float64, device=device) * (math.pi / n_angles))[:, None]
+    s = ((torch.arange(n_det, dtype=torch.float64, device=device) - n_det / 2) * (2.0 * math.sqrt(2.0) / n_det))[None, :]
+    out = torch.zeros((n_angles, n_det), dtype=torch.float64, device=device)
+    cth, sth = torch.cos(th), torch.sin(th)
+    for e in ellipses:
+        c, sn = torch.cos(th - e.psi), torch.sin(th - e.psi)
+        half2 = (e.a * c) ** 2 + (e.b * sn) ** 2
+        t = s - (e.cx * cth + e.cy * sth)
+        rem = torch.clamp(half2 - t * t, min=0.0)
+        out += e.density * 2.0 * e.a * e.b * torch.sqrt(rem) / half2
+    return out
+
+
+def ellipse_values_at(ellipses: list[Ellipse], N: int, rows, cols, sub: int = 4) -> np.ndarray:
+    """``ellipse_image`` at the listed pixels only (same 4 x 4 sub-pixel coverage)."""
+    base, off = _grid(N, sub)
+    y0 = base[np.asarray(rows)]
+    x0 = base[np.asarray(cols)]
+    out = np.zeros(y0.shape)
+    for e in ellipses:
+        c, s = np.cos(e.psi), np.sin(e.psi)
+        acc = np.zeros(y0.shape)
+        for oy in off:
+            y = y0 + oy - e.cy
+            for ox in off:
+                x = x0 + ox - e.cx
+                u = x * c + y * s
+                v = -x * s + y * c
+                acc += ((u / e.a) ** 2 + (v / e.b) ** 2 <= 1.0)
+        out += e.density * acc / (sub * sub)
+    return out
+
+
 def slice_sizes(count: int, seed: int, choices=(256, 512, 1024, 2048, 4096)) -> list[int]:
     """Uneven slice sizes N drawn uniformly from ``choices``."""
     rng = np.random.default_rng(seed)
