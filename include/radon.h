@@ -130,7 +130,8 @@ int radon_backproject_batch(radon_plan plan, const float* d_sinos, float* d_imag
 
 /* Kernel of the theta convolution (the column FFTs of Sections 3 and 5), a performance knob.
  * group 0: the specialised in-place kernel, available when n_theta is a power of two from 256
- * to 8192 (the default there); group 1, 2 or 4: the generic mixed-radix kernel with that many rho
+ * to 8192, or 1372 = 14 x 14 x 7 or 2744 = 14 x 14 x 14 (the default there; 1372 is the length
+ * for 2048 angles and M = 3); group 1, 2 or 4: the generic mixed-radix kernel with that many rho
  * frequencies per CTA (the default otherwise).  Groups 1, 2 and 4 give identical results; group 0
  * differs from them by FP32 rounding only.  RADON_NOT_SUPPORTED if the kernel is unavailable or
  * does not fit. */
@@ -192,7 +193,9 @@ int radon_plan_kernel_launches(radon_plan plan, int op, int* out);
  * device current; make that first call before any stream capture.  The array is shared by all
  * calls on a device and keeps the last call's contents; each call clears what must start at zero.
  * Calls that can overlap on the GPU (different streams, or different host threads) race on the
- * array: order them on one stream or synchronise between them. */
+ * array: order them on one stream or synchronise between them.  The looked-up address is kept for
+ * the life of the process; a cudaDeviceReset on that device invalidates it, so do not call this
+ * entry point on a device after resetting it. */
 #define RADON_STATIC_SCRATCH_BYTES (16u << 20)
 int radon_forward_static_scratch(radon_plan plan, const float* d_image, float* d_sino, void* stream);
 
