@@ -770,6 +770,69 @@ __global__ void __launch_bounds__(TH, MINB) k_columns_fixed(DevPlan p, const flo
   }
 }
 
+// Transposed theta pass of the exact transpose (k_columns_t's work with the specialised
+// transform): the kept rows (centre half plus halo) are placed on their lattice rows (rows that
+// alias when n_theta < n_theta_half + 4 are summed), transformed, multiplied by conj(K),
+// transformed back, and the centre half is stored.
+template <int G>
+struct ColumnLoadT {
+  const float2* y;  // kept rows of this partition, x_pitch apart
+  int x_pitch, nh, nrow, nn, kr0, nc;
+  __device__ __forceinline__ float2 operator()(int row, int g) const {
+    float2 v = make_float2(0.f, 0.f);
+    if (kr0 + g <= nc)
+      for (int jr = (row - nh / 2 + kHaloLo + nn) % nn; jr < nrow; jr += nn)
+        v = cadd(v, y[static_cast<size_t>(jr) * x_pitch + kr0 + g]);
+    return v;
+  }
+};
+template <int G, int NN>
+struct ColumnKernelStoreT {
+  static constexpr bool kShared = true;
+  float2* d;
+  const float2* kern;  // [k_rho][k_theta], k_theta in [0, NN / 2]
+  int kr0, nc;
+  __device__ __forceinline__ void operator()(int row, int g, float2 v) const {
+    const int kt = row <= NN - row ? row : NN - row;
+    const int kr = kr0 + g <= nc ? kr0 + g : nc;
+    d[row * G + g] = cmul(v, cconj(kern[static_cast<size_t>(kr) * (NN / 2 + 1) + kt]));
+  }
+};
+template <int G, int NN>
+struct ColumnStoreT {
+  static constexpr bool kShared = false;
+  float2* x;  // centre-half rows of this partition, x_pitch apart
+  int x_pitch, nh, kr0, nc;
+  __device__ __forceinline__ void operator()(int row, int g, float2 v) const {
+    const int jj = row - nh / 2;
+    if (jj >= 0 && jj < nh && kr0 + g <= nc) x[static_cast<size_t>(jj) * x_pitch + kr0 + g] = v;
+  }
+};
+
+template <int G, int TH, int MINB, int... Rs>
+__global__ void __launch_bounds__(TH, MINB) k_columns_fixed_t(DevPlan p, const float2* __restrict__ kern, int n_items) {
+  constexpr int NN = chain_length<Rs...>();
+  constexpr int NTW = chain_twiddles<Rs...>();
+  extern __shared__ __align__(16) float2 smem[];
+  float2* data = smem;
+  float2* tw = smem + NN * G;
+  stage_table(tw, p.tw_col, NTW, threadIdx.x, blockDim.x);
+  const int ngroups = (p.nc + G) / G;
+  const int nrow = p.nh + kHaloLo + kHaloHi;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int gi = w % ngroups, mb = w / ngroups;
+    const int m = mb % p.M, b = mb / p.M;
+    const int kr0 = gi * G;
+    const ColumnLoadT<G> in{p.yspec + b * p.bs_ys + static_cast<size_t>(m) * nrow * p.x_pitch, p.x_pitch, p.nh, nrow,
+                            NN, kr0, p.nc};
+    const ColumnKernelStoreT<G, NN> mul{data, kern, kr0, p.nc};
+    InplaceChain<NN, G, TH, false, 1, 0, Rs...>::run(tw, in, data, mul, threadIdx.x);
+    const ColumnStoreT<G, NN> out{p.xspec + b * p.bs_x + static_cast<size_t>(m) * p.nh * p.x_pitch, p.x_pitch, p.nh,
+                                  kr0, p.nc};
+    InplaceChain<NN, G, TH, true, 1, 0, Rs...>::run(tw, SmemIn<G>{data}, data, out, threadIdx.x);
+  }
+}
+
 template <int G, int TH, int MINB, int... Rs>
 constexpr bool column_radices_match(const ColumnRadices& c) {
   int i = 0;
@@ -809,6 +872,14 @@ cudaError_t launch_columns_fixed(const DevPlan& p, const float2* kern, cudaStrea
   return cudaSuccess;
 }
 
+template <int G, int TH, int MINB, int... Rs>
+cudaError_t launch_columns_fixed_t(const DevPlan& p, const float2* kern, cudaStream_t st, int batch) {
+  const int n_items = (p.nc + G) / G * p.M * batch;
+  const int grid = n_items < p.col_blocks_t ? n_items : p.col_blocks_t;
+  k_columns_fixed_t<G, TH, MINB, Rs...><<<grid, TH, columns_fixed_smem<G, TH, MINB, Rs...>(), st>>>(p, kern, n_items);
+  return cudaSuccess;
+}
+
 // Raises the kernel's shared memory limit and sizes its persistent grid (resident CTAs).
 template <int G, int TH, int MINB, int... Rs>
 cudaError_t configure_columns_fixed(DevPlan& p, int optin, int n_sm) {
@@ -820,6 +891,11 @@ cudaError_t configure_columns_fixed(DevPlan& p, int optin, int n_sm) {
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TH, smem);
   if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidValue;
   p.col_blocks = per_sm * n_sm;
+  auto* fn_t = k_columns_fixed_t<G, TH, MINB, Rs...>;
+  int per_sm_t = 0;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn_t, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, fn_t, TH, smem);
+  p.col_blocks_t = per_sm_t * n_sm;  // 0: the transpose keeps the generic theta pass
   return e;
 }
 
@@ -1640,7 +1716,7 @@ cudaError_t configure_kernels(DevPlan& p) {
   p.col_group_t = 0;
   for (int G = 4; G >= 1 && !p.col_group_t; G /= 2)
     if (cols_t_smem(p, G) <= static_cast<size_t>(optin)) p.col_group_t = G;
-  p.col_blocks = 0;
+  p.col_blocks = p.col_blocks_t = 0;
   if (p.col_fixed >= 0) {
     int n_sm = 0;
     if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -1747,8 +1823,18 @@ cudaError_t launch_transpose(const DevPlan& p, const float* sino, float* image, 
   hook(12, st);
   k_rows_r2c_t<<<dim3(nrow, p.M, batch), kThreads, rows_smem(p), st>>>(p);
   hook(13, st);
-  const int G = p.col_group_t;
-  k_columns_t<<<dim3((p.nc + 1 + G - 1) / G, p.M, batch), kThreads, cols_t_smem(p, G), st>>>(p, p.k_fwd, G);
+  if (p.col_group == 0 && p.col_fixed >= 0 && p.col_blocks_t > 0) {
+    switch (p.col_fixed) {
+#define RADON_LAUNCH_COLUMN_T(i, ...) \
+  case i: launch_columns_fixed_t<__VA_ARGS__>(p, p.k_fwd, st, batch); break;
+      RADON_COLUMN_KERNELS(RADON_LAUNCH_COLUMN_T)
+#undef RADON_LAUNCH_COLUMN_T
+      default: break;
+    }
+  } else {
+    const int G = p.col_group_t;
+    k_columns_t<<<dim3((p.nc + 1 + G - 1) / G, p.M, batch), kThreads, cols_t_smem(p, G), st>>>(p, p.k_fwd, G);
+  }
   hook(14, st);
   k_rows_c2r_t<<<dim3(p.nh, p.M, batch), kThreads, rows_smem(p), st>>>(p);
   hook(15, st);

@@ -21,6 +21,7 @@ struct DevPlan {
   int col_group;   // generic column kernel: rho frequencies per CTA (4, 2 or 1); 0: specialised kernel
   int col_fixed;   // kColumnRadices index of the specialised column kernel, -1 if none
   int col_blocks;  // persistent grid of the specialised column kernel (resident CTAs on the device)
+  int col_blocks_t; // same for its transposed form (exact transpose); 0: generic theta pass
   int col_group_t; // rho frequencies per CTA of the transposed theta pass (0: does not fit)
   int live_lo, live_hi;  // detector bins with |s| < 1 are exactly [live_lo, live_hi]
   float inv_drho, inv_dphi, inv_aR, d_s;
