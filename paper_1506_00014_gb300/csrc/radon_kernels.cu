@@ -538,7 +538,47 @@ __device__ __forceinline__ void backproject_row_cubic(const DevPlan& p, const fl
   }
 }
 
-__device__ void sample_row_backproject(const DevPlan& p, int b, int m, int jj, float* __restrict__ h) {
+// Cubic back-projection row with the theta interpolation done first: the four theta tap rows and
+// their weights are the same for every rho sample of the row, so they are combined once into one
+// detector row comb[c] = sum_t w_t row_t(c) (a flipped row read at K - c) in shared memory, and each
+// rho sample then takes a 4-tap cubic interpolation in s of that row: 4 taps per sample instead of
+// 16.  The sum runs in the other order than backproject_row_cubic's, so the two agree to FP32
+// rounding.  Taps outside the padded row read zero.  All threads of the CTA call it.
+__device__ __forceinline__ void backproject_row_cubic_comb(const DevPlan& p, const float* const (&rows)[4],
+                                                           const bool (&flip)[4], const float (&wt)[4], int cjx,
+                                                           float Fc, float* __restrict__ h, float* __restrict__ comb) {
+  const int pitch = p.sino_pitch;
+  const int K = p.n_det + 2 * kPad;  // padded index of a flipped tap: K - c
+  for (int c = threadIdx.x; c < pitch; c += blockDim.x) {
+    float acc = 0.f;
+#pragma unroll
+    for (int dt = 0; dt < 4; ++dt) {
+      const int idx = flip[dt] ? K - c : c;  // flip[] is uniform over the CTA
+      const float x = (idx >= 0 && idx < pitch) ? __ldg(rows[dt] + idx) : 0.f;
+      acc = fmaf(wt[dt], x, acc);
+    }
+    comb[c] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < p.N_rho; i += blockDim.x) {
+    const int2 ei = p.bp_e[i];
+    const float F = __int_as_float(ei.y) + Fc;
+    const float fl = floorf(F);
+    const int c0 = ei.x + cjx + static_cast<int>(fl) - 1;  // taps c0 .. c0 + 3
+    float ws[4];
+    bspline_w(F - fl, ws);
+    float acc = 0.f;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int c = c0 + d;
+      acc = fmaf(ws[d], (c >= 0 && c < pitch) ? comb[c] : 0.f, acc);
+    }
+    h[i] = acc;
+  }
+}
+
+__device__ void sample_row_backproject(const DevPlan& p, int b, int m, int jj, float* __restrict__ h,
+                                       float* __restrict__ comb) {
   const int2 th = p.bp_th[m * p.nh + jj];
   const int2 cj = p.bp_c[jj];
   const float Ft = __int_as_float(th.y), Fc = __int_as_float(cj.y);
@@ -564,6 +604,10 @@ __device__ void sample_row_backproject(const DevPlan& p, int b, int m, int jj, f
     flip[dt] = a2 >= na;
     nflip += (dt < ntap && flip[dt]) ? 1 : 0;
     rows[dt] = p.coef_sino + b * p.bs_sino + static_cast<size_t>(flip[dt] ? a2 - na : a2) * pitch;
+  }
+  if (cubic && comb) {
+    backproject_row_cubic_comb(p, rows, flip, wt, cj.x, Fc, h, comb);
+    return;
   }
   if (cubic) {
     if (nflip == 0)
@@ -643,7 +687,9 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
     float2* tws = smem + 2 * nc;
     if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
     tw = p.rows_tw_smem ? tws : p.tw_rho;
-    sample_row_backproject(p, b, m, jj, reinterpret_cast<float*>(bufA));
+    // bufB (free until the FFT) holds the theta-combined detector row when it fits
+    float* comb = p.sino_pitch <= 2 * nc ? reinterpret_cast<float*>(bufB) : nullptr;
+    sample_row_backproject(p, b, m, jj, reinterpret_cast<float*>(bufA), comb);
   } else {  // the row sampled by k_sample_fwd, read as nc complex values
     float2* tws = smem + 2 * nc;
     if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
@@ -1129,6 +1175,8 @@ __global__ void __launch_bounds__(128) k_gather_sino(DevPlan p, float* __restric
   sino[static_cast<size_t>(a) * nd + k] = out;
 }
 
+constexpr int kCombMax = 1024;  // columns of the theta-combined row one scatter CTA may touch
+
 // R# g(x) = sum_m interpolant of partition m at the log-polar coordinates of T_m x.
 __global__ void __launch_bounds__(kPTile * kPTile, 6) k_gather_image(DevPlan p, float* __restrict__ img) {
   const int N = p.N;
@@ -1174,6 +1222,86 @@ __device__ __forceinline__ bool interior_tap(int c, int P) { return c >= kPad &&
 
 __device__ __forceinline__ float* lp_real_rows(const DevPlan& p, int b) {
   return reinterpret_cast<float*>(p.yspec + b * p.bs_ys);
+}
+
+// Transpose of k_gather_sino (cubic) with the theta weights applied last: a sinogram row reads
+// the same four log-polar rows with the same theta weights for every bin, so the CTA's bins
+// first add their rho-weighted values into one shared row over the columns they reach
+// (shared-memory atomics), and that row is then spread onto the four log-polar rows with the theta
+// weights: one global atomic per touched column and row instead of 16 per bin.  Equal to
+// k_scatter_sino up to FP32 rounding.  CTAs whose bins span more than kCombMax columns take the
+// per-bin path.
+__global__ void __launch_bounds__(128) k_scatter_sino_comb(DevPlan p, const float* __restrict__ sino) {
+  __shared__ float comb[kCombMax];
+  __shared__ int red[2];
+  const int a = blockIdx.y, b = blockIdx.z;
+  const int k = blockIdx.x * 128 + threadIdx.x;
+  const int nd = p.n_det;
+  const bool live = k < nd && k >= p.live_lo && k <= p.live_hi;
+  const int4 ang = p.fwd_ang[a];
+  float v = 0.f, ar = 0.f;
+  int c0 = INT_MAX;
+  if (live) {
+    v = __ldg(sino + (static_cast<size_t>(b) * p.n_angles + a) * nd + k) * (p.inv_aR * lp_gain_inv(p));
+    const int4 anc = p.fwd_anc[static_cast<size_t>(a) * p.n_ktiles + k / kKTile];
+    const int n = k - (k / kKTile) * kKTile;
+    const float cr = fmaf(log1pf(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
+    const float fr = floorf(cr);
+    ar = cr - fr;
+    c0 = clampi(anc.x + static_cast<int>(fr) - 1, 0, p.y_pitch - 4);
+  }
+  if (threadIdx.x == 0) {
+    red[0] = INT_MAX;
+    red[1] = INT_MAX;
+  }
+  __syncthreads();
+  const int wmin = __reduce_min_sync(0xffffffffu, c0);
+  const int wmaxn = __reduce_min_sync(0xffffffffu, live ? -c0 : INT_MAX);
+  if ((threadIdx.x & 31) == 0 && wmin != INT_MAX) {
+    atomicMin(red + 0, wmin);
+    atomicMin(red + 1, wmaxn);
+  }
+  __syncthreads();
+  if (red[0] == INT_MAX) return;  // uniform: no live bin
+  const int lo = red[0], W = -red[1] + 3 - lo + 1;
+  float2 w[4];  // .x: theta weights, .y: rho weights (times 6 each)
+  bspline_w6_pair(make_float2(__int_as_float(ang.w), ar), w);
+  const int nrow = p.nh + kHaloLo + kHaloHi, nr = p.N_rho, yp = 2 * p.x_pitch, wrap_end = nr + 2 * kPad;
+  float* y = lp_real_rows(p, b) + static_cast<size_t>(ang.x) * nrow * yp;
+  const int r0 = clampi(ang.z - 1, 0, nrow - 4);
+  if (W > kCombMax) {  // uniform: per-bin taps
+    if (!live || v == 0.f) return;
+#pragma unroll
+    for (int dt = 0; dt < 4; ++dt) {
+      float* row = y + static_cast<size_t>(r0 + dt) * yp;
+      const float vt = v * w[dt].x;
+#pragma unroll
+      for (int dc = 0; dc < 4; ++dc) {
+        const int pc = c0 + dc;
+        if (pc >= wrap_end) continue;
+        int col = pc - kPad;
+        col = col < 0 ? col + nr : (col >= nr ? col - nr : col);
+        atomicAdd(row + col, vt * w[dc].y);
+      }
+    }
+    return;
+  }
+  for (int j = threadIdx.x; j < W; j += blockDim.x) comb[j] = 0.f;
+  __syncthreads();
+  if (live && v != 0.f) {
+#pragma unroll
+    for (int dc = 0; dc < 4; ++dc) atomicAdd(comb + (c0 - lo + dc), v * w[dc].y);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < W; j += blockDim.x) {
+    const float cv = comb[j];
+    const int pc = lo + j;
+    if (cv == 0.f || pc >= wrap_end) continue;
+    int col = pc - kPad;
+    col = col < 0 ? col + nr : (col >= nr ? col - nr : col);
+#pragma unroll
+    for (int dt = 0; dt < 4; ++dt) atomicAdd(y + static_cast<size_t>(r0 + dt) * yp + col, cv * w[dt].x);
+  }
 }
 
 // Transpose of k_gather_sino: g(theta_a, s_k) / a_R is added to the 16 (cubic) or 4 (linear)
@@ -1608,9 +1736,7 @@ void launch_rows_forward(const DevPlan& p, cudaStream_t st, int batch) {
     return;
   }
   const dim3 grid(p.nh, p.M, batch);
-  // the back-projection rows keep the generic transform: with the compiled one its sampling
-  // part ran slower (measured 78 -> 92 us at N = 2048)
-  switch (BACK ? -1 : p.row_fixed) {
+  switch (p.row_fixed) {
 #define RADON_LAUNCH_ROWS_FWD(i, ...) \
   case i: k_rows_fwd<BACK, i><<<grid, kThreads, rows_smem(p), st>>>(p); break;
     RADON_ROW_SEQUENCES(RADON_LAUNCH_ROWS_FWD)
@@ -1819,7 +1945,10 @@ cudaError_t launch_transpose(const DevPlan& p, const float* sino, float* image, 
   if (e == cudaSuccess) e = cudaMemsetAsync(p.coef_img, 0, sizeof(float) * p.bs_img * batch, st);
   if (e != cudaSuccess) return e;
   const int nrow = p.nh + kHaloLo + kHaloHi;
-  k_scatter_sino<<<dim3((p.n_det + 127) / 128, p.n_angles, batch), 128, 0, st>>>(p, sino);
+  if (p.interp == 3 && p.use_tex)  // the transpose of the forward's theta-combined gather
+    k_scatter_sino_comb<<<dim3((p.n_det + 127) / 128, p.n_angles, batch), 128, 0, st>>>(p, sino);
+  else
+    k_scatter_sino<<<dim3((p.n_det + 127) / 128, p.n_angles, batch), 128, 0, st>>>(p, sino);
   hook(12, st);
   k_rows_r2c_t<<<dim3(nrow, p.M, batch), kThreads, rows_smem(p), st>>>(p);
   hook(13, st);

@@ -267,6 +267,22 @@ def test_full_size_backprojection_matches_oracle(rl, full_geo, interp):
     assert _rel(got, ref) < TOL, _rel(got, ref)
 
 
+def test_full_size_four_partitions_match_oracle(rl):
+    """M = 4 at the full single-slice size (the lattice the batch tuner picks for N = 2048:
+    n_theta = 1024, N_rho = 3500): R of the ellipse phantom and R# of the noise sinogram."""
+    geo = geometry.make_geometry(2048, 2048, 3072, 4, 3)
+    plan = rl.radon_plan_create(2048, 2048, 3072, 3, 4)
+    assert (plan.info["n_theta"], plan.info["N_rho"]) == (geo.n_theta, geo.N_rho) == (1024, 3500)
+    f = ellipse_image(2048, random_ellipses(50, 2))
+    got = _gpu_forward(rl, plan, f)
+    ref = logpolar.forward(_f32(f), geo)
+    assert _rel(got, ref) < TOL, _rel(got, ref)
+    g = random_sinogram(2048, 3072, 3)
+    got = _gpu_back(rl, plan, g)
+    ref = logpolar.backproject(_f32(g), geo)
+    assert _rel(got, ref) < TOL, _rel(got, ref)
+
+
 def test_full_size_fbp_matches_oracle(rl, full_geo):
     geo = full_geo[3]
     plan = rl.radon_plan_create(2048, 2048, 3072, 3, 3)
