@@ -118,12 +118,12 @@ int radon_transpose(radon_plan plan, const float* d_sino, float* d_image, void* 
 int radon_transpose_batch(radon_plan plan, const float* d_sinos, float* d_images, int batch, void* stream);
 
 /* Batches of same-size slices.  radon_plan_reserve_batch makes the plan able to process up to
- * max_batch slices in one call: it allocates scratch and texture storage for them, synchronising
- * the device (call it before any stream capture).  It returns RADON_NOT_SUPPORTED when the
- * stacked slices exceed the device's 2-D surface height.  radon_forward_batch /
- * radon_backproject_batch then transform `batch` <= max_batch slices stored back to back
- * ([batch][N][N] images, [batch][n_angles][n_det] sinograms) with the same kernel launches as
- * one slice (radon_plan_kernel_launches); results equal those of per-slice calls. */
+ * max_batch slices in one call: it allocates scratch for them, synchronising the device (call it
+ * before any stream capture), and returns RADON_OUT_OF_MEMORY, keeping the previous capacity, when
+ * the device cannot hold them.  radon_forward_batch / radon_backproject_batch then transform
+ * `batch` <= max_batch slices stored back to back ([batch][N][N] images, [batch][n_angles][n_det]
+ * sinograms) with the same kernel launches as one slice (radon_plan_kernel_launches); results
+ * equal those of per-slice calls. */
 int radon_plan_reserve_batch(radon_plan plan, int max_batch);
 int radon_forward_batch(radon_plan plan, const float* d_images, float* d_sinos, int batch, void* stream);
 int radon_backproject_batch(radon_plan plan, const float* d_sinos, float* d_images, int batch, void* stream);

@@ -15,7 +15,6 @@ struct radon_plan_s {
   void* table_mem = nullptr;
   void* scratch_mem = nullptr;
   size_t table_bytes = 0;
-  cudaArray_t lp_array = nullptr;   // backing store of the log-polar coefficient texture
   float* io_image = nullptr;  // device staging for the host-buffer entry points
   float* io_sino = nullptr;
   // per-stage event timing (radon_profile_enable / radon_profile_read)

@@ -100,43 +100,14 @@ radon::StageHook hook_of(radon_plan_s* p) {
   return h;
 }
 
-// Frees the scratch buffer and the texture storage (the device must be idle).
+// Frees the scratch buffer (the device must be idle).
 void release_scratch(radon_plan_s* p) {
-  radon::DevPlan& d = p->dp;
-  if (d.tex_lp) cudaDestroyTextureObject(d.tex_lp);
-  if (d.surf_lp) cudaDestroySurfaceObject(d.surf_lp);
-  if (p->lp_array) cudaFreeArray(p->lp_array);
   if (p->scratch_mem) cudaFree(p->scratch_mem);
-  d.tex_lp = 0;
-  d.surf_lp = 0;
-  p->lp_array = nullptr;
   p->scratch_mem = nullptr;
 }
 
-// A width x height float CUDA array with a point-sampled, zero-border texture and a surface.
-cudaError_t make_texture(int width, int height, cudaArray_t* arr, cudaTextureObject_t* tex, cudaSurfaceObject_t* surf) {
-  cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
-  cudaError_t e = cudaMallocArray(arr, &fd, width, height, cudaArraySurfaceLoadStore);
-  if (e != cudaSuccess) return e;
-  cudaResourceDesc rd;
-  std::memset(&rd, 0, sizeof(rd));
-  rd.resType = cudaResourceTypeArray;
-  rd.res.array.array = *arr;
-  cudaTextureDesc td;
-  std::memset(&td, 0, sizeof(td));
-  td.addressMode[0] = cudaAddressModeBorder;
-  td.addressMode[1] = cudaAddressModeBorder;
-  td.filterMode = cudaFilterModePoint;
-  td.readMode = cudaReadModeElementType;
-  td.normalizedCoords = 0;
-  e = cudaCreateTextureObject(tex, &rd, &td, nullptr);
-  if (e == cudaSuccess) e = cudaCreateSurfaceObject(surf, &rd);
-  return e;
-}
-
-// Scratch buffers and texture storage for `cap` same-size slices; replaces the previous ones.
-// Slice b of a batch uses the buffers at offset b * (per-slice size) and the log-polar texture
-// rows [b M nrow, (b + 1) M nrow).
+// Scratch buffers for `cap` same-size slices; replaces the previous ones.  Slice b of a batch
+// uses the buffers at offset b * (per-slice size).
 cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
   radon::DevPlan& d = p->dp;
   const int N = d.N, na = d.n_angles, nd = d.n_det;
@@ -146,12 +117,7 @@ cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
   const size_t e_x = static_cast<size_t>(d.M) * d.nh * d.x_pitch;
   const size_t e_ys = static_cast<size_t>(d.M) * nrow * d.x_pitch;
   const size_t e_y = static_cast<size_t>(d.M) * nrow * d.y_pitch;
-  const long long tex_lp_h = static_cast<long long>(cap) * d.M * static_cast<long long>(nrow);
-  int dev = 0, max_h = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxSurface2DHeight, dev);
-  if (e != cudaSuccess) return e;
-  if (cap < 1 || tex_lp_h > max_h) return cudaErrorInvalidValue;
+  if (cap < 1) return cudaErrorInvalidValue;
   size_t sc = 0;
   auto take = [&](size_t bytes) {
     const size_t off = sc;
@@ -168,30 +134,15 @@ cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
   const size_t s_io_img = take(sizeof(float) * static_cast<size_t>(N) * N);
   const size_t s_io_sino = take(sizeof(float) * static_cast<size_t>(na) * nd);
   void* mem = nullptr;
-  cudaArray_t lp_arr = nullptr;
-  cudaTextureObject_t tex_lp = 0;
-  cudaSurfaceObject_t surf_lp = 0;
-  e = cudaMalloc(&mem, sc);
-  if (e == cudaSuccess) e = cudaMemset(mem, 0, sc);
-  if (e == cudaSuccess) e = make_texture(d.y_pitch, static_cast<int>(tex_lp_h), &lp_arr, &tex_lp, &surf_lp);
-  // the array starts undefined: copy zeros (the fresh scratch) into it
-  if (e == cudaSuccess)
-    e = cudaMemcpy2DToArray(lp_arr, 0, 0, static_cast<char*>(mem) + s_y, sizeof(float) * d.y_pitch,
-                            sizeof(float) * d.y_pitch, tex_lp_h, cudaMemcpyDeviceToDevice);
+  cudaError_t e = cudaMalloc(&mem, sc);
+  if (e == cudaSuccess) e = cudaMemset(mem, 0, sc);  // zero borders and pad columns stay zero
   if (e != cudaSuccess) {
-    if (tex_lp) cudaDestroyTextureObject(tex_lp);
-    if (surf_lp) cudaDestroySurfaceObject(surf_lp);
-    if (lp_arr) cudaFreeArray(lp_arr);
     cudaFree(mem);
     return e;
   }
   release_scratch(p);
   char* sb = static_cast<char*>(mem);
   p->scratch_mem = mem;
-  p->lp_array = lp_arr;
-  d.tex_lp = tex_lp;
-  d.surf_lp = surf_lp;
-  d.use_tex = 1;
   d.coef_img = reinterpret_cast<float*>(sb + s_img);
   d.coef_q4 = reinterpret_cast<float4*>(sb + s_q4);
   d.img_quad = 1;
@@ -208,7 +159,7 @@ cudaError_t allocate_scratch(radon_plan_s* p, int cap) {
   d.batch_cap = cap;
   p->io_image = reinterpret_cast<float*>(sb + s_io_img);
   p->io_sino = reinterpret_cast<float*>(sb + s_io_sino);
-  p->info.device_bytes = p->table_bytes + sc + sizeof(float) * static_cast<size_t>(d.y_pitch) * tex_lp_h;
+  p->info.device_bytes = p->table_bytes + sc;
   return cudaSuccess;
 }
 
@@ -463,6 +414,7 @@ int radon_plan_reserve_batch(radon_plan plan, int max_batch) {
   if (max_batch <= plan->dp.batch_cap) return RADON_OK;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = allocate_scratch(plan, max_batch);
+  if (e == cudaErrorMemoryAllocation) cudaGetLastError();  // not sticky: clear it for later launches
   if (e == cudaErrorInvalidValue) return RADON_NOT_SUPPORTED;
   return status_of(e);
 }

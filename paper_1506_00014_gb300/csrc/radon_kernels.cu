@@ -969,13 +969,9 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(DevPlan p) {
   const float2* Z = row_fft<true, SEQ>(bufA, bufB, p, tw);
   const float* h = reinterpret_cast<const float*>(Z);
   float* y = p.ylp + b * p.bs_y + (static_cast<size_t>(m) * nrow + row) * p.y_pitch;
-  const int yrow = (b * p.M + m) * nrow + row;
   for (int c = static_cast<int>(threadIdx.x) - kPad; c < nr + kPad; c += blockDim.x) {
-    int src = c < 0 ? c + nr : (c >= nr ? c - nr : c);
-    if (p.use_tex)
-      surf2Dwrite(h[src], p.surf_lp, (c + kPad) * static_cast<int>(sizeof(float)), yrow);
-    else
-      y[c + kPad] = h[src];
+    const int src = c < 0 ? c + nr : (c >= nr ? c - nr : c);
+    y[c + kPad] = h[src];
   }
 }
 
@@ -1081,13 +1077,9 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv_pipe(DevPlan p, int n_row
     const float* h = reinterpret_cast<const float*>(Z);
     const int b = R / per_slice, mr = R - b * per_slice;  // mr = m nrow + row
     float* y = p.ylp + b * p.bs_y + static_cast<size_t>(mr) * p.y_pitch;
-    const int yrow = b * per_slice + mr;
     for (int c = static_cast<int>(threadIdx.x) - kPad; c < nr + kPad; c += blockDim.x) {
       const int src = c < 0 ? c + nr : (c >= nr ? c - nr : c);
-      if (p.use_tex)
-        surf2Dwrite(h[src], p.surf_lp, (c + kPad) * static_cast<int>(sizeof(float)), yrow);
-      else
-        y[c + kPad] = h[src];
+      y[c + kPad] = h[src];
     }
     __syncthreads();
   }
@@ -1099,37 +1091,13 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv_pipe(DevPlan p, int n_row
 
 // Interpolant of partition m's log-polar coefficients at (halo row It + at, padded column
 // Ir + ar), times lp_gain(p) (36 for cubic: the weights are taken times 6 per axis and the caller
-// applies 1 / lp_gain once); taps are clamped into the array.  With use_tex the coefficients are read with
-// tex2Dgather from the CUDA array (partition m occupies rows [m nrow, (m+1) nrow)).
+// applies 1 / lp_gain once); taps are clamped into the array.  The coefficients are plain global
+// rows (measured faster than gathers from a texture copy, which also needed a surface store per
+// value in the inverse rho pass).
 __device__ __forceinline__ float lp_gain_inv(const DevPlan& p) { return p.interp == 3 ? 1.f / 36.f : 1.f; }
 
 __device__ __forceinline__ float sample_lp(const DevPlan& p, int b, int m, int It, float at, int Ir, float ar) {
   const int nrow = p.nh + kHaloLo + kHaloHi;
-  const int pm = b * p.M + m;  // partition block in the (slice, partition)-stacked texture
-  if (p.use_tex) {
-    const cudaTextureObject_t t = p.tex_lp;
-    if (p.interp == 3) {
-      float2 w[4];  // .x: theta weights, .y: rho weights
-      bspline_w6_pair(make_float2(at, ar), w);
-      const float wt[4] = {w[0].x, w[1].x, w[2].x, w[3].x}, wr[4] = {w[0].y, w[1].y, w[2].y, w[3].y};
-      const float y0 = static_cast<float>(pm * nrow + clampi(It - 1, 0, nrow - 4)) + 1.f, y1 = y0 + 2.f;
-      const float x0 = static_cast<float>(clampi(Ir - 1, 0, p.y_pitch - 4)) + 1.f, x1 = x0 + 2.f;
-      const float4 g00 = tex2Dgather<float4>(t, x0, y0, 0);
-      const float4 g10 = tex2Dgather<float4>(t, x1, y0, 0);
-      const float4 g01 = tex2Dgather<float4>(t, x0, y1, 0);
-      const float4 g11 = tex2Dgather<float4>(t, x1, y1, 0);
-      const float r0 = fmaf(wr[0], g00.w, fmaf(wr[1], g00.z, fmaf(wr[2], g10.w, wr[3] * g10.z)));
-      const float r1 = fmaf(wr[0], g00.x, fmaf(wr[1], g00.y, fmaf(wr[2], g10.x, wr[3] * g10.y)));
-      const float r2 = fmaf(wr[0], g01.w, fmaf(wr[1], g01.z, fmaf(wr[2], g11.w, wr[3] * g11.z)));
-      const float r3 = fmaf(wr[0], g01.x, fmaf(wr[1], g01.y, fmaf(wr[2], g11.x, wr[3] * g11.y)));
-      return fmaf(wt[0], r0, fmaf(wt[1], r1, fmaf(wt[2], r2, wt[3] * r3)));
-    }
-    const float4 g = tex2Dgather<float4>(t, static_cast<float>(clampi(Ir, 0, p.y_pitch - 2)) + 1.f,
-                                         static_cast<float>(pm * nrow + clampi(It, 0, nrow - 2)) + 1.f, 0);
-    const float v0 = fmaf(ar, g.z - g.w, g.w);
-    const float v1 = fmaf(ar, g.y - g.x, g.x);
-    return fmaf(at, v1 - v0, v0);
-  }
   const float* __restrict__ y = p.ylp + b * p.bs_y + static_cast<size_t>(m) * nrow * p.y_pitch;
   if (p.interp == 3) {
     float2 w[4];  // .x: theta weights, .y: rho weights
@@ -1945,7 +1913,7 @@ cudaError_t launch_transpose(const DevPlan& p, const float* sino, float* image, 
   if (e == cudaSuccess) e = cudaMemsetAsync(p.coef_img, 0, sizeof(float) * p.bs_img * batch, st);
   if (e != cudaSuccess) return e;
   const int nrow = p.nh + kHaloLo + kHaloHi;
-  if (p.interp == 3 && p.use_tex)  // the transpose of the forward's theta-combined gather
+  if (p.interp == 3)
     k_scatter_sino_comb<<<dim3((p.n_det + 127) / 128, p.n_angles, batch), 128, 0, st>>>(p, sino);
   else
     k_scatter_sino<<<dim3((p.n_det + 127) / 128, p.n_angles, batch), 128, 0, st>>>(p, sino);

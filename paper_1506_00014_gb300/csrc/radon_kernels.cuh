@@ -50,9 +50,6 @@ struct DevPlan {
   float* coef_img;     // (N + 2 kPad)^2, zero border
   float4* coef_q4;     // same grid; element (r, c) holds coefficients (r, c .. c+3) (zero past the edge)
   int img_quad;        // 1: forward sampling reads coef_q4 (one 16-byte load per tap row)
-  int use_tex;         // 1: the log-polar coefficients are read through tex_lp
-  cudaTextureObject_t tex_lp;    // log-polar coefficients, M (nh + 4) rows x y_pitch columns
-  cudaSurfaceObject_t surf_lp;   // write view (filled by the inverse rho FFT)
   int rows_tw_smem;    // 1: row kernels stage the rho twiddles in shared memory
   int rows_pipe_fwd;   // > 0: resident CTAs of the persistent forward rho transform (0: one CTA per row)
   int rows_pipe_inv;   // > 0: resident CTAs of the persistent inverse rho transform
@@ -64,7 +61,7 @@ struct DevPlan {
   float* sino_tmp;     // n_angles x n_det (filtered sinogram for FBP)
   // batches of same-size slices: slice b = blockIdx.z uses scratch at these strides (elements)
   size_t bs_img, bs_sino, bs_x, bs_ys, bs_y;
-  int batch_cap;       // slices the scratch and the textures hold
+  int batch_cap;       // slices the scratch holds
   int n_filt;          // FBP: zero-padded real FFT length along s
   int filt_tw_smem;    // 1: the FBP row kernel stages its twiddles in shared memory
   RadixList rad_filt;

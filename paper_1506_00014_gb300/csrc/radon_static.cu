@@ -71,7 +71,6 @@ extern "C" int radon_forward_static_scratch(radon_plan plan, const float* d_imag
   char* b = static_cast<char*>(base);
   radon::DevPlan p = p0;
   p.coef_img = reinterpret_cast<float*>(b + o_img);
-  p.use_tex = 0;   // the plan's texture array is not scratch: read the static buffers instead
   p.img_quad = 0;  // no room for the quad layout: 16 scalar loads per sample
   p.batch_cap = 1;
   p.xspec = reinterpret_cast<float2*>(b + o_x);

@@ -49,10 +49,16 @@ def test_batch_capacity_limits(rl):
     y = torch.zeros((2, 64, 96), device="cuda")
     with pytest.raises(rl.RadonError):  # capacity is 1 until reserved
         rl.radon_forward_batch(plan, x, y)
-    big = rl.radon_plan_create(4096, 4096, 6144, 3, 3)
-    with pytest.raises(rl.RadonError) as err:  # 20 x 4099 texture rows exceed the surface height
-        rl.radon_plan_reserve_batch(big, 20)
-    assert err.value.status == 5  # RADON_NOT_SUPPORTED
+    big = rl.radon_plan_create(1024, 1024, 1536, 3, 3)
+    with pytest.raises(rl.RadonError) as err:  # ~10^6 slices of scratch (about 200 TB) cannot be allocated
+        rl.radon_plan_reserve_batch(big, 1 << 20)
+    assert err.value.status == 2  # RADON_OUT_OF_MEMORY
+    # the plan keeps its previous capacity and still runs
+    f = torch.zeros((1024, 1024), device="cuda")
+    s = torch.full((1024, 1536), float("nan"), device="cuda")
+    rl.radon_forward(big, f, s)
+    torch.cuda.synchronize()
+    assert float(s.abs().max()) == 0.0
     few = rl.radon_plan_create(4096, 64, 96, 3, 3)  # few angles: many sub-angles per coarse angle
     assert few.info["r"] > 32  # more than one anchor per lane in the sampling warps
 
