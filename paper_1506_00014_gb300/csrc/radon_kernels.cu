@@ -820,16 +820,16 @@ __global__ void __launch_bounds__(TH, MINB) k_columns_fixed(DevPlan p, const flo
 // transform): the kept rows (centre half plus halo) are placed on their lattice rows (rows that
 // alias when n_theta < n_theta_half + 4 are summed), transformed, multiplied by conj(K),
 // transformed back, and the centre half is stored.
-template <int G>
+// The specialised lengths are at least 256, so n_theta >= n_theta_half + 4 rows: each lattice row
+// holds at most one kept row (no aliasing to sum), and the load is one predicated read, which the
+// pass issues together with its other loads.
+template <int G, int NN>
 struct ColumnLoadT {
   const float2* y;  // kept rows of this partition, x_pitch apart
-  int x_pitch, nh, nrow, nn, kr0, nc;
+  int x_pitch, nh, nrow, kr0, nc;
   __device__ __forceinline__ float2 operator()(int row, int g) const {
-    float2 v = make_float2(0.f, 0.f);
-    if (kr0 + g <= nc)
-      for (int jr = (row - nh / 2 + kHaloLo + nn) % nn; jr < nrow; jr += nn)
-        v = cadd(v, y[static_cast<size_t>(jr) * x_pitch + kr0 + g]);
-    return v;
+    const int jr = (row - nh / 2 + kHaloLo + NN) % NN;
+    return (jr < nrow && kr0 + g <= nc) ? y[static_cast<size_t>(jr) * x_pitch + kr0 + g] : make_float2(0.f, 0.f);
   }
 };
 template <int G, int NN>
@@ -858,6 +858,7 @@ struct ColumnStoreT {
 template <int G, int TH, int MINB, int... Rs>
 __global__ void __launch_bounds__(TH, MINB) k_columns_fixed_t(DevPlan p, const float2* __restrict__ kern, int n_items) {
   constexpr int NN = chain_length<Rs...>();
+  static_assert(NN >= 8, "n_theta = 2 n_theta_half >= n_theta_half + 4 kept rows (ColumnLoadT)");
   constexpr int NTW = chain_twiddles<Rs...>();
   extern __shared__ __align__(16) float2 smem[];
   float2* data = smem;
@@ -869,8 +870,8 @@ __global__ void __launch_bounds__(TH, MINB) k_columns_fixed_t(DevPlan p, const f
     const int gi = w % ngroups, mb = w / ngroups;
     const int m = mb % p.M, b = mb / p.M;
     const int kr0 = gi * G;
-    const ColumnLoadT<G> in{p.yspec + b * p.bs_ys + static_cast<size_t>(m) * nrow * p.x_pitch, p.x_pitch, p.nh, nrow,
-                            NN, kr0, p.nc};
+    const ColumnLoadT<G, NN> in{p.yspec + b * p.bs_ys + static_cast<size_t>(m) * nrow * p.x_pitch, p.x_pitch, p.nh,
+                                nrow, kr0, p.nc};
     const ColumnKernelStoreT<G, NN> mul{data, kern, kr0, p.nc};
     InplaceChain<NN, G, TH, false, 1, 0, Rs...>::run(tw, in, data, mul, threadIdx.x);
     const ColumnStoreT<G, NN> out{p.xspec + b * p.bs_x + static_cast<size_t>(m) * p.nh * p.x_pitch, p.x_pitch, p.nh,
