@@ -710,6 +710,37 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
   }
 }
 
+// Back-projection rows, persistent: one CTA per resident slot walks the rows (m, jj) of every
+// slice, staging the rho twiddles once instead of once per row; each row is sampled (theta-combined
+// when the combined detector row fits in bufB), transformed and written as k_rows_fwd<true> does.
+template <int SEQ>
+__global__ void __launch_bounds__(kThreads) k_rows_bp_persistent(DevPlan p, int n_rows) {
+  extern __shared__ __align__(16) float2 smem[];
+  const int nc = p.nc;
+  float2* bufA = smem;
+  float2* bufB = smem + nc;
+  float2* tws = smem + 2 * nc;  // rows_bp_persistent is launched only when the twiddles fit (rows_tw_smem)
+  stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
+  float* comb = p.sino_pitch <= 2 * nc ? reinterpret_cast<float*>(bufB) : nullptr;
+  const int per_slice = p.M * p.nh;
+  for (int R = blockIdx.x; R < n_rows; R += gridDim.x) {
+    const int b = R / per_slice, mj = R - b * per_slice, m = mj / p.nh, jj = mj - m * p.nh;
+    __syncthreads();  // the previous row's buffers (and, the first time, the staged twiddles)
+    sample_row_backproject(p, b, m, jj, reinterpret_cast<float*>(bufA), comb);
+    __syncthreads();
+    const float2* Z = row_fft<false, SEQ>(bufA, bufB, p, tws);
+    float2* out = p.xspec + b * p.bs_x + static_cast<size_t>(mj) * p.x_pitch;
+    for (int k = threadIdx.x; k <= nc; k += blockDim.x) {
+      const float2 zk = Z[k == nc ? 0 : k];
+      const float2 zc = cconj(Z[k == 0 ? 0 : nc - k]);
+      const float2 ev = cscale(cadd(zk, zc), 0.5f);
+      const float2 dv = cscale(csub(zk, zc), 0.5f);
+      const float2 od = make_float2(dv.y, -dv.x);  // -i (Z_k - conj Z_{n-k}) / 2
+      out[k] = cadd(ev, cmul(p.tw_r2c[k], od));
+    }
+  }
+}
+
 // FFT along theta of col_group rho frequencies, multiply by the kernel, inverse FFT, keep the
 // centre half plus the halo rows.
 __global__ void __launch_bounds__(kThreads) k_columns(DevPlan p, const float2* __restrict__ kern) {
@@ -1692,6 +1723,18 @@ size_t cols_t_smem(const DevPlan& p, int G) { return (2 * static_cast<size_t>(G)
 
 template <bool BACK>
 void launch_rows_forward(const DevPlan& p, cudaStream_t st, int batch) {
+  if (BACK && p.rows_bp_blocks > 0) {
+    const int n_rows = p.M * p.nh * batch;
+    const int blocks = n_rows < p.rows_bp_blocks ? n_rows : p.rows_bp_blocks;
+    switch (p.row_fixed) {
+#define RADON_LAUNCH_ROWS_BP(i, ...) \
+  case i: k_rows_bp_persistent<i><<<blocks, kThreads, rows_smem(p), st>>>(p, n_rows); break;
+      RADON_ROW_SEQUENCES(RADON_LAUNCH_ROWS_BP)
+#undef RADON_LAUNCH_ROWS_BP
+      default: k_rows_bp_persistent<-1><<<blocks, kThreads, rows_smem(p), st>>>(p, n_rows); break;
+    }
+    return;
+  }
   if (!BACK && p.rows_pipe_fwd > 0) {
     const int n_rows = p.M * p.nh * batch;
     const int blocks = n_rows < p.rows_pipe_fwd ? n_rows : p.rows_pipe_fwd;
@@ -1765,6 +1808,15 @@ cudaError_t configure_rows_pipe(KF* kf, KI* ki, int optin, size_t smem, int* per
   if ((e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_fwd, kf, kThreads, smem)) != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_inv, ki, kThreads, smem);
+}
+
+// Raise a persistent kernel's dynamic shared memory limit to the device maximum and report how
+// many of its CTAs fit on one SM with `smem` bytes.
+template <class K>
+cudaError_t configure_persistent(K* k, int optin, size_t smem, int* per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, kThreads, smem);
 }
 
 cudaError_t configure_kernels(DevPlan& p) {
@@ -1842,6 +1894,21 @@ cudaError_t configure_kernels(DevPlan& p) {
     if (e != cudaSuccess) return e;
     p.rows_pipe_fwd = per_sm_fwd * n_sm;
     p.rows_pipe_inv = per_sm_inv * n_sm;
+  }
+  // persistent back-projection rows: when the twiddles are staged in shared memory
+  p.rows_bp_blocks = 0;
+  if (p.rows_tw_smem) {
+    int n_sm = 0, per_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    switch (p.row_fixed) {
+#define RADON_CONFIGURE_ROWS_BP(i, ...) \
+  case i: e = configure_persistent(k_rows_bp_persistent<i>, optin, rows_smem(p), &per_sm); break;
+      RADON_ROW_SEQUENCES(RADON_CONFIGURE_ROWS_BP)
+#undef RADON_CONFIGURE_ROWS_BP
+      default: e = configure_persistent(k_rows_bp_persistent<-1>, optin, rows_smem(p), &per_sm);
+    }
+    if (e != cudaSuccess) return e;
+    p.rows_bp_blocks = per_sm * n_sm;
   }
   return cudaSuccess;
 }

@@ -53,6 +53,7 @@ struct DevPlan {
   int rows_tw_smem;    // 1: row kernels stage the rho twiddles in shared memory
   int rows_pipe_fwd;   // > 0: resident CTAs of the persistent forward rho transform (0: one CTA per row)
   int rows_pipe_inv;   // > 0: resident CTAs of the persistent inverse rho transform
+  int rows_bp_blocks;  // > 0: resident CTAs of the persistent back-projection rows
   int row_fixed;       // kRowRadices index of the compiled row transform, -1: generic
   float* coef_sino;    // n_angles x sino_pitch, zero border
   float2* xspec;       // M x nh x x_pitch
