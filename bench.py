@@ -935,7 +935,8 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_once():
+def run_once(transpose: bool = False):
+    """One untimed R and R# (or, with ``transpose``, one exact transpose R^T) of the workload."""
     import numpy as np
     import torch
 
@@ -947,10 +948,14 @@ def run_once():
     g = torch.from_numpy(random_sinogram(N_ANGLES, N_DET, 3).astype(np.float32)).cuda()
     s = torch.empty((N_ANGLES, N_DET), dtype=torch.float32, device="cuda")
     i = torch.empty((N, N), dtype=torch.float32, device="cuda")
-    rl.radon_forward(plan, f, s)
-    rl.radon_backproject(plan, g, i)
+    if transpose:
+        rl.radon_transpose(plan, g, i)
+    else:
+        rl.radon_forward(plan, f, s)
+        rl.radon_backproject(plan, g, i)
     torch.cuda.synchronize()
-    print(json.dumps({"once": WORKLOAD, "sino_sum": float(s.double().sum()), "img_sum": float(i.double().sum())}))
+    print(json.dumps({"once": WORKLOAD, "transpose": transpose, "sino_sum": float(s.double().sum()) if not transpose
+                      else None, "img_sum": float(i.double().sum())}))
 
 
 def main():
@@ -964,9 +969,11 @@ def main():
                     help="skip the batched (96 uneven slices) and least-squares (64 slices) comparisons")
     ap.add_argument("--once", action="store_true",
                     help="one untimed R + R# on the workload (for profiler captures); prints a short line")
+    ap.add_argument("--once-transpose", action="store_true",
+                    help="one untimed exact transpose R^T on the workload (for profiler captures)")
     args = ap.parse_args()
-    if args.once:
-        run_once()
+    if args.once or args.once_transpose:
+        run_once(transpose=args.once_transpose)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

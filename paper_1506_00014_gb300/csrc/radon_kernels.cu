@@ -1485,26 +1485,33 @@ __device__ __forceinline__ bool scatter_corner(int interp, const float4& a, floa
 }
 
 // Adds the SPAN x SPAN tap block with top-left padded index (rt, ct) and weights wr x wc to the
-// box (origin (r0, c0), W x H) or to coef_img; taps in the zero border are dropped.
+// box (origin (r0, c0), W x H) or to coef_img.  Into the box every tap goes, border ones included:
+// the flush drops the box cells that lie in the zero border, which is the same as dropping those
+// taps here, without two tests per tap.  The block lies inside the box by construction (the box is
+// the bounding rectangle of these corners); one test per block guards that.  Straight into coef_img
+// the border taps are dropped one by one.
 template <int SPAN>
 __device__ __forceinline__ void scatter_block(const float (&wc)[SPAN], const float (&wr)[SPAN], int rt, int ct, int P,
                                               bool use_box, float* box, int W, int H, int r0, int c0,
                                               float* __restrict__ img) {
+  if (use_box) {
+    const int by = rt - r0, bx = ct - c0;
+    if (by < 0 || by + SPAN > H || bx < 0 || bx + SPAN > W) return;
+    float* b0 = box + by * W + bx;
+#pragma unroll
+    for (int dr = 0; dr < SPAN; ++dr) {
+      float* row = b0 + dr * W;
+#pragma unroll
+      for (int dc = 0; dc < SPAN; ++dc) atomicAdd(row + dc, wr[dr] * wc[dc]);
+    }
+    return;
+  }
 #pragma unroll
   for (int dr = 0; dr < SPAN; ++dr) {
     if (!interior_tap(rt + dr, P)) continue;
 #pragma unroll
-    for (int dc = 0; dc < SPAN; ++dc) {
-      if (!interior_tap(ct + dc, P)) continue;
-      const float val = wr[dr] * wc[dc];
-      if (use_box) {
-        const int by = rt + dr - r0, bx = ct + dc - c0;
-        if (static_cast<unsigned>(by) < static_cast<unsigned>(H) && static_cast<unsigned>(bx) < static_cast<unsigned>(W))
-          atomicAdd(box + by * W + bx, val);
-      } else {
-        atomicAdd(img + static_cast<size_t>(rt + dr) * P + (ct + dc), val);
-      }
-    }
+    for (int dc = 0; dc < SPAN; ++dc)
+      if (interior_tap(ct + dc, P)) atomicAdd(img + static_cast<size_t>(rt + dr) * P + (ct + dc), wr[dr] * wc[dc]);
   }
 }
 
@@ -1646,7 +1653,8 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_scatter_fwd(DevPlan p) {
     const float v = box[idx];
     if (v != 0.f) {
       const int by = idx / W, bx = idx - by * W;
-      atomicAdd(img + static_cast<size_t>(r0 + by) * P + (c0 + bx), v);
+      if (interior_tap(r0 + by, P) && interior_tap(c0 + bx, P))  // the zero border stays zero
+        atomicAdd(img + static_cast<size_t>(r0 + by) * P + (c0 + bx), v);
     }
   }
 }
