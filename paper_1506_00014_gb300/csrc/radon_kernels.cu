@@ -1167,7 +1167,7 @@ __global__ void __launch_bounds__(128) k_gather_sino(DevPlan p, float* __restric
     const int4 ang = p.fwd_ang[a];
     const int4 anc = p.fwd_anc[static_cast<size_t>(a) * p.n_ktiles + k / kKTile];
     const int n = k - (k / kKTile) * kKTile;
-    const float cr = fmaf(log1pf(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
+    const float cr = fmaf(small_log1p(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
     const float fr = floorf(cr);
     out = sample_lp(p, b, ang.x, ang.z, __int_as_float(ang.w), anc.x + static_cast<int>(fr), cr - fr) *
           (p.inv_aR * lp_gain_inv(p));
@@ -1245,7 +1245,7 @@ __global__ void __launch_bounds__(128) k_scatter_sino_comb(DevPlan p, const floa
     v = __ldg(sino + (static_cast<size_t>(b) * p.n_angles + a) * nd + k) * (p.inv_aR * lp_gain_inv(p));
     const int4 anc = p.fwd_anc[static_cast<size_t>(a) * p.n_ktiles + k / kKTile];
     const int n = k - (k / kKTile) * kKTile;
-    const float cr = fmaf(log1pf(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
+    const float cr = fmaf(small_log1p(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
     const float fr = floorf(cr);
     ar = cr - fr;
     c0 = clampi(anc.x + static_cast<int>(fr) - 1, 0, p.y_pitch - 4);
@@ -1317,7 +1317,7 @@ __global__ void __launch_bounds__(128) k_scatter_sino(DevPlan p, const float* __
   const int4 ang = p.fwd_ang[a];
   const int4 anc = p.fwd_anc[static_cast<size_t>(a) * p.n_ktiles + k / kKTile];
   const int n = k - (k / kKTile) * kKTile;
-  const float cr = fmaf(log1pf(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
+  const float cr = fmaf(small_log1p(static_cast<float>(n) * __int_as_float(anc.z)), p.inv_drho, __int_as_float(anc.y));
   const float fr = floorf(cr);
   const int It = ang.z, Ir = anc.x + static_cast<int>(fr);
   const float at = __int_as_float(ang.w), ar = cr - fr;
