@@ -117,6 +117,18 @@ int radon_fbp(radon_plan plan, const float* d_sino, float* d_image, int filter, 
 int radon_transpose(radon_plan plan, const float* d_sino, float* d_image, void* stream);
 int radon_transpose_batch(radon_plan plan, const float* d_sinos, float* d_images, int batch, void* stream);
 
+/* Uneven batches (Section 7 batches slices of a volume to fill the GPU): `count` slices, slice i
+ * transformed by plans[i] from d_images[i] to d_sinos[i] (radon_forward_multi) or from d_sinos[i]
+ * to d_images[i] (radon_backproject_multi), launched in order on one stream.  Plans may differ in
+ * size; a plan may appear several times (its scratch is reused in stream order, so one plan must
+ * not also run on another stream meanwhile).  Every plan and pointer is checked before the first
+ * launch: RADON_INVALID_ARG launches nothing.  A launch error returns its status after the slices
+ * before it were launched.  The call can be captured in a CUDA graph like the per-slice calls. */
+int radon_forward_multi(const radon_plan* plans, const float* const* d_images, float* const* d_sinos, int count,
+                        void* stream);
+int radon_backproject_multi(const radon_plan* plans, const float* const* d_sinos, float* const* d_images, int count,
+                            void* stream);
+
 /* Batches of same-size slices.  radon_plan_reserve_batch makes the plan able to process up to
  * max_batch slices in one call: it allocates scratch for them, synchronising the device (call it
  * before any stream capture), and returns RADON_OUT_OF_MEMORY, keeping the previous capacity, when

@@ -14,10 +14,12 @@ from .binding import (  # noqa: F401
     radon_backproject,
     radon_backproject_batch,
     radon_backproject_host,
+    radon_backproject_multi,
     radon_fbp,
     radon_forward,
     radon_forward_batch,
     radon_forward_host,
+    radon_forward_multi,
     radon_forward_static_scratch,
     radon_geometry,
     radon_kernel_quadrant,

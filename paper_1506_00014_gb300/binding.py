@@ -40,7 +40,8 @@ EXPORTED = (
     "radon_geometry", "radon_kernel_quadrant", "radon_status_string", "radon_profile_enable",
     "radon_profile_read", "radon_forward_static_scratch", "radon_plan_reserve_batch",
     "radon_forward_batch", "radon_backproject_batch", "radon_plan_set_column_group",
-    "radon_plan_kernel_launches", "radon_transpose", "radon_transpose_batch",
+    "radon_plan_kernel_launches", "radon_transpose", "radon_transpose_batch", "radon_forward_multi",
+    "radon_backproject_multi",
 )
 
 RADON_NUM_STAGES = 18
@@ -89,6 +90,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.radon_plan_kernel_launches.argtypes = [_c_void_p, _c_int, P(_c_int)]
     for name in ("radon_forward_batch", "radon_backproject_batch", "radon_transpose_batch"):
         getattr(lib, name).argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_void_p]
+    for name in ("radon_forward_multi", "radon_backproject_multi"):
+        getattr(lib, name).argtypes = [P(_c_void_p), P(_c_void_p), P(_c_void_p), _c_int, _c_void_p]
     lib.radon_profile_enable.argtypes = [_c_void_p, _c_int]
     lib.radon_profile_read.argtypes = [_c_void_p, P(ctypes.c_double), P(_c_int)]
     lib.radon_status_string.argtypes = [_c_int]
@@ -299,6 +302,30 @@ def radon_backproject_batch(plan: RadonPlan, sinos, images, stream=None):
                                           _dev(images, (b,) + plan.image_shape, "images"), b, _stream(stream, sinos)),
            "radon_backproject_batch")
     return images
+
+
+def _multi(name: str, plans, ins, outs, in_shape, out_shape, stream):
+    n = len(plans)
+    if len(ins) != n or len(outs) != n:
+        raise ValueError(f"{name}: plans, inputs and outputs differ in length")
+    arr_p = (ctypes.c_void_p * n)(*[pl.handle for pl in plans])
+    arr_i = (ctypes.c_void_p * n)(*[_dev(t, in_shape(pl), "input") for pl, t in zip(plans, ins)])
+    arr_o = (ctypes.c_void_p * n)(*[_dev(t, out_shape(pl), "output") for pl, t in zip(plans, outs)])
+    st = _stream(stream, ins[0]) if n else None
+    _check(getattr(load(), name)(arr_p, arr_i, arr_o, n, st), name)
+    return outs
+
+
+def radon_forward_multi(plans, images, sinos, stream=None):
+    """Slice i: images[i] -> sinos[i] with plans[i] (plans may differ in size), one stream."""
+    return _multi("radon_forward_multi", plans, images, sinos, lambda pl: pl.image_shape, lambda pl: pl.sino_shape,
+                  stream)
+
+
+def radon_backproject_multi(plans, sinos, images, stream=None):
+    """Slice i: sinos[i] -> images[i] with plans[i] (plans may differ in size), one stream."""
+    return _multi("radon_backproject_multi", plans, sinos, images, lambda pl: pl.sino_shape,
+                  lambda pl: pl.image_shape, stream)
 
 
 def radon_transpose_batch(plan: RadonPlan, sinos, images, stream=None):

@@ -433,6 +433,44 @@ int radon_backproject_batch(radon_plan plan, const float* d_sinos, float* d_imag
       radon::launch_backproject(plan->dp, d_sinos, d_images, static_cast<cudaStream_t>(stream), hook_of(plan), batch));
 }
 
+namespace {
+
+// Checks every slice of an uneven batch before anything is launched.
+bool multi_args_ok(const radon_plan* plans, const void* const* in, const void* const* out, int count) {
+  if (!plans || !in || !out || count < 0) return false;
+  for (int i = 0; i < count; ++i)
+    if (!plans[i] || !in[i] || !out[i] || !on_plan_device(plans[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+int radon_forward_multi(const radon_plan* plans, const float* const* d_images, float* const* d_sinos, int count,
+                        void* stream) {
+  if (!multi_args_ok(plans, reinterpret_cast<const void* const*>(d_images),
+                     reinterpret_cast<const void* const*>(d_sinos), count))
+    return RADON_INVALID_ARG;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) {
+    const cudaError_t e = radon::launch_forward(plans[i]->dp, d_images[i], d_sinos[i], st, hook_of(plans[i]));
+    if (e != cudaSuccess) return status_of(e);
+  }
+  return RADON_OK;
+}
+
+int radon_backproject_multi(const radon_plan* plans, const float* const* d_sinos, float* const* d_images, int count,
+                            void* stream) {
+  if (!multi_args_ok(plans, reinterpret_cast<const void* const*>(d_sinos),
+                     reinterpret_cast<const void* const*>(d_images), count))
+    return RADON_INVALID_ARG;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) {
+    const cudaError_t e = radon::launch_backproject(plans[i]->dp, d_sinos[i], d_images[i], st, hook_of(plans[i]));
+    if (e != cudaSuccess) return status_of(e);
+  }
+  return RADON_OK;
+}
+
 int radon_plan_set_column_group(radon_plan plan, int group) {
   if (!plan || (group != 0 && group != 1 && group != 2 && group != 4)) return RADON_INVALID_ARG;
   radon::DevPlan d = plan->dp;

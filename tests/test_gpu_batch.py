@@ -153,3 +153,43 @@ def test_uneven_batch_tunes_the_partition_count_and_matches_the_oracle(rl):
         ref_b = logpolar.backproject(got_s.astype(np.float64), geo)
         got_b = ub.image(i).cpu().numpy()
         assert np.linalg.norm(got_b - ref_b) / np.linalg.norm(ref_b) < 1e-5
+
+
+def test_multi_plan_calls_equal_per_slice_calls(rl):
+    """radon_forward_multi / radon_backproject_multi over plans of different sizes (one plan used
+    twice) equal per-slice calls bit for bit, also when replayed from a CUDA graph."""
+    sizes = [(64, 64, 96), (96, 100, 150), (64, 64, 96), (128, 128, 192)]
+    plans = {}
+    for n, na, nd in sizes:
+        plans.setdefault((n, na, nd), rl.radon_plan_create(n, na, nd, 3, 3))
+    pl = [plans[s] for s in sizes]
+    imgs = [_t(ellipse_image(n, random_ellipses(6, 70 + i))) for i, (n, _, _) in enumerate(sizes)]
+    sins = [_t(random_sinogram(na, nd, 80 + i)) for i, (_, na, nd) in enumerate(sizes)]
+    out_s = [torch.empty((na, nd), device="cuda") for _, na, nd in sizes]
+    out_i = [torch.empty((n, n), device="cuda") for n, _, _ in sizes]
+    rl.radon_forward_multi(pl, imgs, out_s)
+    rl.radon_backproject_multi(pl, sins, out_i)
+    torch.cuda.synchronize()
+    for k, (n, na, nd) in enumerate(sizes):
+        one_s = torch.empty((na, nd), device="cuda")
+        one_i = torch.empty((n, n), device="cuda")
+        rl.radon_forward(pl[k], imgs[k], one_s)
+        rl.radon_backproject(pl[k], sins[k], one_i)
+        torch.cuda.synchronize()
+        assert torch.equal(one_s, out_s[k]) and torch.equal(one_i, out_i[k])
+    ref_s = [t.clone() for t in out_s]
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        rl.radon_forward_multi(pl, imgs, out_s)
+    torch.cuda.current_stream().wait_stream(side)
+    with torch.cuda.graph(graph):
+        rl.radon_forward_multi(pl, imgs, out_s)
+    for t in out_s:
+        t.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(out_s, ref_s))
+    with pytest.raises(ValueError):
+        rl.radon_forward_multi(pl, imgs[:2], out_s)

@@ -113,6 +113,10 @@ def test_every_entry_point_rejects_null_arguments_without_a_gpu(lib):
     for name in ("radon_forward_batch", "radon_backproject_batch", "radon_transpose_batch"):
         assert getattr(cdll, name)(None, None, None, 1, None) == 1, name
     assert cdll.radon_fbp(None, None, None, 0, None) == 1
+    for name in ("radon_forward_multi", "radon_backproject_multi"):
+        assert getattr(cdll, name)(None, None, None, 1, None) == 1, name
+        null = (ctypes.c_void_p * 2)(None, None)  # a list holding NULL plans is rejected before any launch
+        assert getattr(cdll, name)(null, null, null, 2, None) == 1, name
     assert cdll.radon_plan_kernel_launches(None, 3, None) == 1
     assert cdll.radon_plan_reserve_batch(None, 2) == 1
     assert cdll.radon_plan_set_column_group(None, 1) == 1
