@@ -103,6 +103,8 @@ __device__ __forceinline__ float small_log1p(float u) {
 // inside the array read it directly; border tiles map every index through the extension.
 
 constexpr int kPfRows = 32, kPfCols = 64, kPfSeg = 8;
+// the row pass (kPfRows + 2 kFirHalf rows) takes longer segments: fewer warm-up steps per output
+constexpr int kPfSegRow = 16;
 constexpr int kPfInR = kPfRows + 2 * kFirHalf, kPfInC = kPfCols + 2 * kFirHalf;
 
 // Sources of the pre-filter.  Each gives the tile input (direct / extended reads), says when a
@@ -207,17 +209,18 @@ struct CoefSource {
 // -6 z / (1 - z^2) z^|n| = sqrt(3) z^|n|).  The zero states sit kFirHalf samples outside the
 // segment, so the response is cut at z^15 ~ 2.7e-9, as a 29-tap truncated FIR would be, at 8
 // operations per coefficient instead of 29.
-__device__ __forceinline__ void segment_prefilter(float (&w)[kPfSeg + 2 * kFirHalf], float (&c)[kPfSeg]) {
+template <int SEG>
+__device__ __forceinline__ void segment_prefilter(float (&w)[SEG + 2 * kFirHalf], float (&c)[SEG]) {
   constexpr float z = -0.267949192431122706f;  // sqrt(3) - 2
   constexpr float g = -6.f * z;
-  constexpr int W = kPfSeg + 2 * kFirHalf;
+  constexpr int W = SEG + 2 * kFirHalf;
 #pragma unroll
   for (int k = 1; k < W; ++k) w[k] = fmaf(z, w[k - 1], w[k]);
   float v = w[W - 1];
 #pragma unroll
   for (int k = W - 2; k >= kFirHalf; --k) {
     v = fmaf(z, v, w[k]);
-    if (k < kFirHalf + kPfSeg) c[k - kFirHalf] = g * v;
+    if (k < kFirHalf + SEG) c[k - kFirHalf] = g * v;
   }
 }
 
@@ -293,16 +296,16 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
     }
     return;
   }
-  // along rows: kPfInR rows x (kPfCols / kPfSeg) segments
-  for (int task = tid; task < kPfInR * (kPfCols / kPfSeg); task += kThreads) {
-    const int ly = task / (kPfCols / kPfSeg), sx = (task - ly * (kPfCols / kPfSeg)) * kPfSeg;
-    float w[kPfSeg + 2 * kFirHalf];
+  // along rows: kPfInR rows x (kPfCols / kPfSegRow) segments
+  for (int task = tid; task < kPfInR * (kPfCols / kPfSegRow); task += kThreads) {
+    const int ly = task / (kPfCols / kPfSegRow), sx = (task - ly * (kPfCols / kPfSegRow)) * kPfSegRow;
+    float w[kPfSegRow + 2 * kFirHalf];
 #pragma unroll
-    for (int t = 0; t < kPfSeg + 2 * kFirHalf; ++t) w[t] = s_in[ly][sx + t];
-    float c[kPfSeg];
-    segment_prefilter(w, c);
+    for (int t = 0; t < kPfSegRow + 2 * kFirHalf; ++t) w[t] = s_in[ly][sx + t];
+    float c[kPfSegRow];
+    segment_prefilter<kPfSegRow>(w, c);
 #pragma unroll
-    for (int t = 0; t < kPfSeg; ++t) s_mid[ly][sx + t] = c[t];
+    for (int t = 0; t < kPfSegRow; ++t) s_mid[ly][sx + t] = c[t];
   }
   __syncthreads();
   // along columns: kPfCols columns x (kPfRows / kPfSeg) segments
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
     for (int t = 0; t < kPfSeg + 2 * kFirHalf; ++t) w[t] = s_mid[sy + t][lx];
     const int gc = ocol + lx;
     float c[kPfSeg];
-    segment_prefilter(w, c);
+    segment_prefilter<kPfSeg>(w, c);
 #pragma unroll
     for (int t = 0; t < kPfSeg; ++t) {
       const float acc = c[t];
