@@ -140,6 +140,54 @@ def stage_bytes(info):
     }
 
 
+def sample_fwd_fine_samples(info) -> int:
+    """Fine samples the forward sampling reads (cubic: 16 taps each): per partition m, angular row
+    jj and sub-angle q, the rho indices whose 4 x 4 tap block lies inside the padded coefficient
+    array and within 16 + 1.5 pixels of the disc (the rule the plan's sampling ranges follow)."""
+    import numpy as np
+
+    n, mm, nh, r, nr = info["N"], info["n_partitions"], info["n_theta_half"], info["r"], info["N_rho"]
+    a_R, beta, d_phi, d_rho = info["a_R"], info["beta"], info["d_phi"], info["d_rho"]
+    pad, margin = 3, 16
+    S = n / (2.0 * a_R)
+    P = n + 2.0 * pad
+    lo_b, hi_b = 1.0 + 1e-3, P - 2.0 - 1e-3
+    cz, Rd = pad + n / 2.0, n / 2.0 + margin + 1.5
+    jj = np.arange(nh)[:, None]
+    q = np.arange(r)[None, :]
+    total = 0
+    for m in range(mm):
+        C0 = n / 2.0 - (1.0 - a_R) * math.cos(m * beta) * S + pad
+        R0 = n / 2.0 - (1.0 - a_R) * math.sin(m * beta) * S + pad
+        phi = (jj + nh // 2 - nh) * d_phi + (q - 0.5 * (r - 1)) * d_phi / r
+        Cv, Rv = np.cos(phi + m * beta) * S, np.sin(phi + m * beta) * S
+        tl = np.zeros_like(Cv)
+        th = np.full_like(Cv, 1e300)
+        for x0, v in ((C0, Cv), (R0, Rv)):
+            with np.errstate(divide="ignore", invalid="ignore"):
+                a, b = (lo_b - x0) / v, (hi_b - x0) / v
+            ok = v != 0.0
+            tl = np.where(ok, np.maximum(tl, np.minimum(a, b)), tl)
+            th = np.where(ok, np.minimum(th, np.maximum(a, b)), np.where((x0 < lo_b) | (x0 > hi_b), -1.0, th))
+        dx, dy = C0 - cz, R0 - cz
+        A = Cv * Cv + Rv * Rv
+        B = 2.0 * (dx * Cv + dy * Rv)
+        Cq = dx * dx + dy * dy - Rd * Rd
+        disc = B * B - 4.0 * A * Cq
+        sq = np.sqrt(np.maximum(disc, 0.0))
+        tl = np.maximum(tl, (-B - sq) / (2.0 * A))
+        th = np.where(disc < 0.0, -1.0, np.minimum(th, (-B + sq) / (2.0 * A)))
+        live = (th > tl) & (th > 0.0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            il = np.where(tl > 0.0, np.log(np.where(tl > 0.0, tl, 1.0)) / d_rho + nr - 1, -1.0)
+            ih = np.log(np.where(th > 0.0, th, 1.0)) / d_rho + nr - 1
+        ilo = np.maximum(0.0, np.ceil(il))
+        ihi = np.minimum(nr - 1.0, np.floor(ih))
+        cnt = np.where(live & (ihi >= ilo), ihi - ilo + 1, 0.0)
+        total += int(cnt.sum())
+    return total
+
+
 def live_bin_count(n_det: int) -> int:
     """Detector bins with |s| < 1 (exact integer test 2 (2k - n_det)^2 < n_det^2)."""
     return sum(1 for k in range(n_det) if 2 * (2 * k - n_det) ** 2 < n_det * n_det)
@@ -701,6 +749,17 @@ def run_ours(args):
     summary = ncu.get(dom)
     traffic = summary[0] if summary else None
     pb = pair_bytes(info)
+    l1_roofline = None
+    if dom == "sample_fwd" and INTERP == 3:
+        # the binding unit's own roofline: the tap bytes the L1 data path must deliver to registers
+        # (fine samples x 16 taps x 4 B) against n_SM x 128 B per clock at the sampled SM clock
+        fine = sample_fwd_fine_samples(info)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        l1_peak = n_sm * 128 * mhz * 1e6 / 1e9
+        l1_ach = 64 * fine / (dom_ms / 1e3) / 1e9
+        l1_roofline = {"fine_samples": fine, "bytes": 64 * fine, "n_sm": n_sm, "bytes_per_clock_per_sm": 128,
+                       "sm_mhz": mhz, "achieved": l1_ach, "peak": l1_peak, "unit": "GB/s", "frac": l1_ach / l1_peak}
 
     # the linear-interpolation variant of the same workload (same timing rules, fewer steps)
     plan_lin = rl.radon_plan_create(N, N_ANGLES, N_DET, 1, M)
@@ -724,49 +783,81 @@ def run_ours(args):
               "value": whole_job_rate(world, _samples_per_step(), 1, lin_ms / 1e3), "unit": UNIT}
     del plan_lin
 
-    # end to end through the host-buffer C ABI entry points (pinned host memory)
-    h_f = torch.from_numpy(f).pin_memory()
-    h_g = torch.from_numpy(g).pin_memory()
-    h_s = torch.empty((N_ANGLES, N_DET), dtype=torch.float32).pin_memory()
-    h_i = torch.empty((N, N), dtype=torch.float32).pin_memory()
-    # R and R# of a step from two host threads, each with its own plan and stream (the calls
-    # block until their result is in host memory; ctypes releases the GIL while they run)
+    # end to end through the host-buffer C ABI entry points (pinned host memory).  Two pipelines,
+    # each an R thread and an R# thread with their own plans and streams, take alternate steps:
+    # one step's host copies overlap the other step's kernels.  Each call blocks until its result
+    # is in host memory (ctypes releases the GIL while it runs); a pipeline starts its next step
+    # only after both calls of its previous step returned.
     from concurrent.futures import ThreadPoolExecutor
 
-    side_e2e = torch.cuda.Stream(dev)
-    pool = ThreadPoolExecutor(max_workers=1)
+    h_f = torch.from_numpy(f).pin_memory()
+    h_g = torch.from_numpy(g).pin_memory()
+    lanes = []
+    for li in range(2):
+        lanes.append({
+            "plan_r": plan if li == 0 else rl.radon_plan_create(N, N_ANGLES, N_DET, INTERP, M),
+            "plan_b": plan_bp if li == 0 else rl.radon_plan_create(N, N_ANGLES, N_DET, INTERP, M),
+            "st_r": stream if li == 0 else torch.cuda.Stream(dev),
+            "st_b": torch.cuda.Stream(dev),
+            "h_s": torch.empty((N_ANGLES, N_DET), dtype=torch.float32).pin_memory(),
+            "h_i": torch.empty((N, N), dtype=torch.float32).pin_memory(),
+        })
+    pool = ThreadPoolExecutor(max_workers=4)
 
-    def pair_host():
-        fut = pool.submit(rl.radon_backproject_host, plan_bp, h_g, h_i, side_e2e)
-        rl.radon_forward_host(plan, h_f, h_s, stream)
-        fut.result()
+    def submit_pair(ln):
+        return (pool.submit(rl.radon_forward_host, ln["plan_r"], h_f, ln["h_s"], ln["st_r"]),
+                pool.submit(rl.radon_backproject_host, ln["plan_b"], h_g, ln["h_i"], ln["st_b"]))
+
+    def run_host(n_steps, n_lanes):
+        pending = [None] * n_lanes
+        for k in range(n_steps):
+            li = k % n_lanes
+            if pending[li] is not None:
+                for fut in pending[li]:
+                    fut.result()
+            pending[li] = submit_pair(lanes[li])
+        for pend in pending:
+            if pend is not None:
+                for fut in pend:
+                    fut.result()
 
     def pair_host_serial():
-        rl.radon_forward_host(plan, h_f, h_s, stream)
-        rl.radon_backproject_host(plan, h_g, h_i, stream)
+        rl.radon_forward_host(plan, h_f, lanes[0]["h_s"], stream)
+        rl.radon_backproject_host(plan, h_g, lanes[0]["h_i"], stream)
 
+    run_host(4, 2)
+    run_host(2, 1)
     for _ in range(2):
-        pair_host()
         pair_host_serial()
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        pair_host()
+    run_host(args.steps, 2)
     e2e_s = reduce_max(time.perf_counter() - t0, dist if world > 1 else None, dev)
+    t0 = time.perf_counter()
+    run_host(n_aux, 1)
+    e2e_one_s = reduce_max(time.perf_counter() - t0, dist if world > 1 else None, dev)
     t0 = time.perf_counter()
     for _ in range(n_aux):
         pair_host_serial()
     e2e_serial_s = reduce_max(time.perf_counter() - t0, dist if world > 1 else None, dev)
     pool.shutdown()
+    e2e_out = (lanes[0]["h_s"].numpy().copy(), lanes[0]["h_i"].numpy().copy(),
+               lanes[1]["h_s"].numpy().copy(), lanes[1]["h_i"].numpy().copy())
+    for ln in lanes[1:]:
+        del ln["plan_r"], ln["plan_b"]
     e2e = {
         "value": whole_job_rate(world, _samples_per_step(), args.steps, e2e_s),
         "unit": UNIT,
         "h2d_bytes_per_step": 4 * (N * N + N_ANGLES * N_DET),
         "d2h_bytes_per_step": 4 * (N_ANGLES * N_DET + N * N),
-        "api": "radon_forward_host and radon_backproject_host from two host threads (one plan and stream each)",
+        "api": "radon_forward_host and radon_backproject_host; two pipelines (an R thread and an R# thread "
+               "each, own plans and streams) take alternate steps",
+        "one_pipeline_value": whole_job_rate(world, _samples_per_step(), n_aux, e2e_one_s),
         "serial_value": whole_job_rate(world, _samples_per_step(), n_aux, e2e_serial_s),
+        "pipelines_equal": bool(np.array_equal(e2e_out[0], e2e_out[2]) and np.array_equal(e2e_out[1], e2e_out[3])),
     }
+    h_s, h_i = e2e_out[0], e2e_out[1]
 
     extras = {}
     if world == 1 and not args.no_extras:
@@ -783,13 +874,13 @@ def run_ours(args):
     err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, (ref_s, ref_i) = cpu_baseline(f, g)
-        err = {"R": rel_l2(h_s.numpy(), ref_s), "R#": rel_l2(h_i.numpy(), ref_i), "tolerance": 1e-5,
+        err = {"R": rel_l2(h_s, ref_s), "R#": rel_l2(h_i, ref_i), "tolerance": 1e-5,
                "oracle": "FP64 log-polar oracle (Algorithms 1 and 2, dense DFTs), same inputs", "metric": "relative L2"}
         from oracle import geometry as _geometry
 
         err["vs_direct_sampled"] = err_vs_direct(
             _geometry.make_geometry(N, N_ANGLES, N_DET, M, INTERP), f, g,
-            {"cuda": (h_s.numpy(), h_i.numpy()), "logpolar_oracle": (ref_s, ref_i)})
+            {"cuda": (h_s, h_i), "logpolar_oracle": (ref_s, ref_i)})
         _, (lin_s, lin_i) = cpu_baseline(f, g, interp=1)
         linear["err_vs_oracle"] = {"R": rel_l2(lin_out[0], lin_s), "R#": rel_l2(lin_out[1], lin_i), "tolerance": 1e-5,
                                    "oracle": "FP64 log-polar oracle, linear interpolation, same inputs",
@@ -823,6 +914,7 @@ def run_ours(args):
             "binding_units_ncu": None if summary is None else {
                 "l1tex_pct_of_peak": summary[1], "issue_pct_of_peak": summary[2],
                 "note": "DRAM throughput is a few percent of peak; L1/TEX and issue bind this kernel"},
+            "l1": l1_roofline,
             "pair": {
                 "bytes": pb["pair"], "bytes_R": pb["R"], "bytes_R#": pb["R#"],
                 "model": "B_R = 4N^2 + 4 n_angles n_det + 4 S_c + |K|, B_R# = 4 n_angles n_live + 4N^2 + 4 S_c + |K|, "

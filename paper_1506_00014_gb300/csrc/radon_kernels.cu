@@ -507,6 +507,105 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_sample_fwd(DevPlan p) {
   if (i1 < p.N_rho) h[i1] = acc1 * e1.x * scale;
 }
 
+// Forward sampling, cubic, quad layout, with each load instruction spread over consecutive fine
+// angles (the same outputs as k_sample_fwd<true>).  The r sub-angles of kSampleWarps adjacent
+// rows are 8 r equally spaced fine angles; a CTA of R warps takes them all for 64 rho samples.
+// Warp w owns fine angles 8 w .. 8 w + 7 and lane 4 a + o the fine angle 8 w + a at rho offsets
+// o, o + 4, ..., so one load instruction reads a 4 (rho) x 8 (fine angle) block of samples: about
+// as far apart across the rays as along them, which touches fewer L1 lines than 32 samples along
+// one ray.  Each lane keeps its fine angle's anchors and rho range in registers.  The fine
+// samples go to shared memory; a second phase sums each output's r sub-angles and applies
+// e^rho / r and the 1/36 of the weights taken times 6.
+constexpr int kArcStride = 68;  // floats per fine angle in shared memory: a store's 32 lanes hit distinct banks
+template <int R, int PITCH>
+__global__ void __launch_bounds__(R * 32, 36 / R) k_sample_fwd_arc(DevPlan p) {
+  __shared__ float sval[kSampleWarps * R][kArcStride];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tile0 = 2 * blockIdx.x, m = blockIdx.z % p.M, b = blockIdx.z / p.M;
+  const int jj0 = blockIdx.y * kSampleWarps;
+  const int f = 8 * warp + (lane >> 2), o = lane & 3;  // fine angle within the CTA, rho offset
+  const int jl = f / R, q = f - jl * R;
+  const bool row_ok = jj0 + jl < p.nh;
+  const int base = tile0 * kETile;
+  const int P = PITCH > 0 ? PITCH : p.img_pitch;
+  float4 a0 = make_float4(1.f, 0.f, 1.f, 0.f), a1 = a0;
+  float2 d = make_float2(0.f, 0.f);
+  int2 rg = make_int2(1, 0);  // empty range
+  if (row_ok) {
+    const size_t rq = (static_cast<size_t>(m) * p.nh + jj0 + jl) * R + q;
+    const float4 cs = p.fwd_row[rq];
+    const float4 um = p.fwd_m[m];
+    const int ne = p.n_eanc;
+    const float2 ea0 = p.fwd_eanc[tile0];
+    const float2 ea1 = p.fwd_eanc[tile0 + 1 < ne ? tile0 + 1 : tile0];
+    float ch, cl, rh, rl;
+    df_mul_add(ea0.x, ea0.y, cs.x, cs.y, um.x, um.y, &ch, &cl);
+    df_mul_add(ea0.x, ea0.y, cs.z, cs.w, um.z, um.w, &rh, &rl);
+    float Ic = floorf(ch), Ir = floorf(rh);
+    a0 = make_float4(Ic, (ch - Ic) + cl, Ir, (rh - Ir) + rl);
+    df_mul_add(ea1.x, ea1.y, cs.x, cs.y, um.x, um.y, &ch, &cl);
+    df_mul_add(ea1.x, ea1.y, cs.z, cs.w, um.z, um.w, &rh, &rl);
+    Ic = floorf(ch);
+    Ir = floorf(rh);
+    a1 = make_float4(Ic, (ch - Ic) + cl, Ir, (rh - Ir) + rl);
+    d = make_float2(cs.x, cs.z);
+    rg = p.fwd_rng[rq];
+  }
+  const float4* __restrict__ img = p.coef_q4 + b * p.bs_img;
+  float* sv = sval[f];
+  // warp-uniform: does any lane of the warp have a sample in this CTA's 64 rho indices?
+  const bool any = __any_sync(0xffffffffu, rg.y >= base && rg.x <= base + 2 * kETile - 1);
+#pragma unroll 1
+  for (int t = 0; t < 2 * kETile / 4; t += 2) {
+    const int i0 = base + 4 * t + o, i1 = i0 + 4;  // same anchor tile: t and t + 1 lie on one side of 8
+    const bool ok0 = any && i0 >= rg.x && i0 <= rg.y, ok1 = any && i1 >= rg.x && i1 <= rg.y;
+    if (!__any_sync(0xffffffffu, ok0 || ok1)) {
+      sv[4 * t + o] = 0.f;
+      sv[4 * t + 4 + o] = 0.f;
+      continue;
+    }
+    const float4 a = t < kETile / 4 ? a0 : a1;
+    const float e0 = ok0 ? p.fwd_e[i0].y : 0.f, e1 = ok1 ? p.fwd_e[i1].y : 0.f;
+    const float Fc0 = fmaf(e0, d.x, a.y), Fr0 = fmaf(e0, d.y, a.w);
+    const float Fc1 = fmaf(e1, d.x, a.y), Fr1 = fmaf(e1, d.y, a.w);
+    const float fc0 = floorf(Fc0), fr0 = floorf(Fr0), fc1 = floorf(Fc1), fr1 = floorf(Fr1);
+    // padded tap-block corners; samples out of range read element (1, 1) and are dropped
+    const int ic0 = ok0 ? static_cast<int>(a.x + fc0) : 1, ir0 = ok0 ? static_cast<int>(a.z + fr0) : 1;
+    const int ic1 = ok1 ? static_cast<int>(a.x + fc1) : 1, ir1 = ok1 ? static_cast<int>(a.z + fr1) : 1;
+    const float4* p0 = img + static_cast<unsigned>(ir0 * P + ic0) - (P + 1);
+    const float4* p1 = img + static_cast<unsigned>(ir1 * P + ic1) - (P + 1);
+    float4 v0[4], v1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v0[k] = __ldg(p0 + k * P);
+      v1[k] = __ldg(p1 + k * P);
+    }
+    float2 wc[4], wr[4];  // .x: sample i0, .y: sample i1
+    bspline_w6_pair(make_float2(Fc0 - fc0, Fc1 - fc1), wc);
+    bspline_w6_pair(make_float2(Fr0 - fr0, Fr1 - fr1), wr);
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      s0 = fmaf(wr[k].x, fmaf(wc[0].x, v0[k].x, fmaf(wc[1].x, v0[k].y, fmaf(wc[2].x, v0[k].z, wc[3].x * v0[k].w))), s0);
+      s1 = fmaf(wr[k].y, fmaf(wc[0].y, v1[k].x, fmaf(wc[1].y, v1[k].y, fmaf(wc[2].y, v1[k].z, wc[3].y * v1[k].w))), s1);
+    }
+    sv[4 * t + o] = ok0 ? s0 : 0.f;
+    sv[4 * t + 4 + o] = ok1 ? s1 : 0.f;
+  }
+  __syncthreads();
+  // outputs (row jl, rho base + il): the sum of the row's R fine samples
+  for (int idx = threadIdx.x; idx < kSampleWarps * 2 * kETile; idx += R * 32) {
+    const int rl = idx / (2 * kETile), il = idx - rl * (2 * kETile);
+    const int jj = jj0 + rl, i = base + il;
+    if (jj >= p.nh || i >= p.N_rho) continue;
+    float acc = 0.f;
+#pragma unroll
+    for (int qq = 0; qq < R; ++qq) acc += sval[rl * R + qq][il];
+    float* h = reinterpret_cast<float*>(p.yspec + b * p.bs_ys + (static_cast<size_t>(m) * p.nh + jj) * p.x_pitch);
+    h[i] = acc * p.fwd_e[i].x * (1.f / 36.f);
+  }
+}
+
 // Back-projection: G(phi_j, rho_i) = g~(phi_j + m beta, (e^rho_i - (1 - a_R) cos phi_j) / a_R).
 // The theta taps (rows of the extended sinogram, flips, weights) are the same for the whole row;
 // a flipped row (theta + pi) is read at k -> n_det - k, i.e. with reversed s weights.  FLIPS:
@@ -1732,6 +1831,21 @@ size_t scatter_fwd_smem(const DevPlan& p) {
 size_t cols_smem(const DevPlan& p) { return (2 * static_cast<size_t>(p.col_group) + 1) * p.n_theta * sizeof(float2); }
 size_t cols_t_smem(const DevPlan& p, int G) { return (2 * static_cast<size_t>(G) + 1) * p.n_theta * sizeof(float2); }
 
+// Forward sampling with fine-angle blocks for r = R sub-angles (tabulated pitches compiled in).
+template <int R>
+void launch_sample_arc(const DevPlan& p, dim3 grid, cudaStream_t st) {
+  switch (p.img_pitch) {
+#define RADON_LAUNCH_ARC(n)                                          \
+  case n + 2 * kPad:                                                 \
+    k_sample_fwd_arc<R, n + 2 * kPad><<<grid, R * 32, 0, st>>>(p);  \
+    return;
+    RADON_SAMPLE_PITCHES(RADON_LAUNCH_ARC)
+#undef RADON_LAUNCH_ARC
+    default:
+      k_sample_fwd_arc<R, 0><<<grid, R * 32, 0, st>>>(p);
+  }
+}
+
 template <bool BACK>
 void launch_rows_forward(const DevPlan& p, cudaStream_t st, int batch) {
   if (BACK && p.rows_bp_blocks > 0) {
@@ -1937,7 +2051,13 @@ cudaError_t launch_forward(const DevPlan& p, const float* image, float* sino, cu
                                       kThreads, 0, st>>>(p, isrc, p.N, p.N, p.coef_img, p.img_pitch, kPad, p.bs_img);
   hook(0, st);
   const dim3 sgrid((p.n_eanc + 1) / 2, (p.nh + kSampleWarps - 1) / kSampleWarps, p.M * batch);
-  if (p.img_quad && p.interp == 3) {
+  if (p.img_quad && p.interp == 3 && p.r == 5) {
+    launch_sample_arc<5>(p, sgrid, st);
+  } else if (p.img_quad && p.interp == 3 && p.r == 4) {
+    launch_sample_arc<4>(p, sgrid, st);
+  } else if (p.img_quad && p.interp == 3 && p.r == 6) {
+    launch_sample_arc<6>(p, sgrid, st);
+  } else if (p.img_quad && p.interp == 3) {
     switch (p.img_pitch) {
 #define RADON_LAUNCH_SAMPLE(n)                                                                    \
   case n + 2 * kPad:                                                                              \

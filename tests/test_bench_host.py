@@ -76,3 +76,34 @@ def test_direct_oracle_sampling_runs_and_reports_each_result():
     assert out["a"]["R"] < 0.05  # the method against exact line integrals of the same interpolant
     assert abs(out["a"]["R"] - out["b"]["R"]) < 1e-5 and abs(out["a"]["R#"] - out["b"]["R#"]) < 1e-5
     assert "8 angles x 16 live bins" in out["sample"]
+
+
+def test_fine_sample_count_matches_a_per_sample_scan():
+    """The forward sampling's fine-sample count (used for its L1 roofline) equals a direct scan of
+    every (partition, angular row, sub-angle, rho index): the tap block inside the padded array and
+    within 16 + 1.5 pixels of the disc."""
+    import math
+
+    import numpy as np
+
+    geo = binding.radon_geometry(64, 48, 96, 3, 3)
+    n, mm, nh, r, nr = geo["N"], geo["n_partitions"], geo["n_theta_half"], geo["r"], geo["N_rho"]
+    S = n / (2.0 * geo["a_R"])
+    P = n + 6.0
+    lo_b, hi_b = 1.0 + 1e-3, P - 2.0 - 1e-3
+    cz, Rd = 3 + n / 2.0, n / 2.0 + 17.5
+    t = np.exp((np.arange(nr) - nr + 1) * geo["d_rho"])
+    count = 0
+    for m in range(mm):
+        C0 = n / 2.0 - (1.0 - geo["a_R"]) * math.cos(m * geo["beta"]) * S + 3
+        R0 = n / 2.0 - (1.0 - geo["a_R"]) * math.sin(m * geo["beta"]) * S + 3
+        for jj in range(nh):
+            for q in range(r):
+                phi = (jj + nh // 2 - nh) * geo["d_phi"] + (q - 0.5 * (r - 1)) * geo["d_phi"] / r
+                col = C0 + t * math.cos(phi + m * geo["beta"]) * S
+                row = R0 + t * math.sin(phi + m * geo["beta"]) * S
+                ok = (col >= lo_b) & (col <= hi_b) & (row >= lo_b) & (row <= hi_b)
+                ok &= (col - cz) ** 2 + (row - cz) ** 2 <= Rd * Rd
+                count += int(ok.sum())
+    assert bench.sample_fwd_fine_samples(geo) == count
+    assert count > 0

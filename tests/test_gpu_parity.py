@@ -68,6 +68,8 @@ CASES = [
     (96, 1536, 150, 3, 3),   # n_theta = 1024 (16 x 8 x 8)
     (64, 2048, 96, 3, 3),    # n_theta = 1372 (14 x 14 x 7, 392 threads)
     (64, 4096, 96, 3, 3),    # n_theta = 2744 (14 x 14 x 14, 2 columns per work item)
+    (120, 180, 170, 3, 3),   # r = 4 sub-angles (1.5 N angles), ragged image tiles
+    (100, 100, 150, 3, 4),   # r = 6 sub-angles, n_theta_half = 28: a partial group of 8 rows
 ]
 
 
