@@ -248,35 +248,46 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
     if constexpr (QUAD) {
       const int P = p.img_pitch;
       float4* q4 = p.coef_q4 + b * p.bs_img;
-      for (int idx = tid; idx < kPfRows * kPfQuads; idx += kThreads) {
-        const int y = idx / kPfQuads, lx = idx - y * kPfQuads;
-        const int gr = orow + y, c = qcol + lx;
-        if (gr < n_rows && c < P) q4[static_cast<size_t>(gr + kPad) * P + c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int y = tid >> 5; y < kPfRows; y += kThreads / 32) {
+        const int gr = orow + y;
+        if (gr >= n_rows) break;
+        float4* dst = q4 + static_cast<size_t>(gr + kPad) * P + qcol;
+        for (int lx = tid & 31; lx < kPfQuads && qcol + lx < P; lx += 32) dst[lx] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     } else {
-      for (int idx = tid; idx < kPfRows * kPfCols; idx += kThreads) {
-        const int y = idx / kPfCols, lx = idx - y * kPfCols;
-        const int gr = orow + y, gc = ccol + lx;
-        if (gr < n_rows && gc < n_cols) out[static_cast<size_t>(gr + out_r0) * out_pitch + gc + Src::kOutPad] = 0.f;
+      for (int y = tid >> 5; y < kPfRows; y += kThreads / 32) {
+        const int gr = orow + y;
+        if (gr >= n_rows) break;
+        float* dst = out + static_cast<size_t>(gr + out_r0) * out_pitch + ccol + Src::kOutPad;
+        for (int lx = tid & 31; lx < kPfCols && ccol + lx < n_cols; lx += 32) dst[lx] = 0.f;
       }
     }
     return;
   }
   if (src.interior(r0, r0 + kPfInR, c0, c0 + kPfInC)) {
+    // warp w reads rows w, w + 8, ... and lane l columns l, l + 32, l + 64 (no index division);
     // all loads of this thread are issued before the first shared-memory store
-    constexpr int kPer = (kPfInR * kPfInC + kThreads - 1) / kThreads;
-    float v[kPer];
+    constexpr int kWarpsPf = kThreads / 32;
+    constexpr int kRowIt = (kPfInR + kWarpsPf - 1) / kWarpsPf, kColIt = (kPfInC + 31) / 32;
+    const int lane = tid & 31, warp = tid >> 5;
+    float v[kRowIt][kColIt];
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int idx = tid + k * kThreads;
-      const int ly = idx / kPfInC, lx = idx - ly * kPfInC;
-      v[k] = idx < kPfInR * kPfInC ? src.direct(r0 + ly, c0 + lx) : 0.f;
+    for (int i = 0; i < kRowIt; ++i) {
+      const int ly = warp + i * kWarpsPf;
+#pragma unroll
+      for (int j = 0; j < kColIt; ++j) {
+        const int lx = lane + 32 * j;
+        v[i][j] = (ly < kPfInR && lx < kPfInC) ? src.direct(r0 + ly, c0 + lx) : 0.f;
+      }
     }
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int idx = tid + k * kThreads;
-      const int ly = idx / kPfInC, lx = idx - ly * kPfInC;
-      if (idx < kPfInR * kPfInC) s_in[ly][lx] = v[k];
+    for (int i = 0; i < kRowIt; ++i) {
+      const int ly = warp + i * kWarpsPf;
+#pragma unroll
+      for (int j = 0; j < kColIt; ++j) {
+        const int lx = lane + 32 * j;
+        if (ly < kPfInR && lx < kPfInC) s_in[ly][lx] = v[i][j];
+      }
     }
   } else {
     for (int idx = tid; idx < kPfInR * kPfInC; idx += kThreads) {
@@ -296,9 +307,11 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
     }
     return;
   }
-  // along rows: kPfInR rows x (kPfCols / kPfSegRow) segments
+  // along rows: kPfInR rows x (kPfCols / kPfSegRow) segments; consecutive threads take
+  // consecutive rows of one segment, so their shared-memory accesses (row strides kPfInC + 1 and
+  // kPfCols + 1, both odd) fall into distinct banks
   for (int task = tid; task < kPfInR * (kPfCols / kPfSegRow); task += kThreads) {
-    const int ly = task / (kPfCols / kPfSegRow), sx = (task - ly * (kPfCols / kPfSegRow)) * kPfSegRow;
+    const int seg = task / kPfInR, ly = task - seg * kPfInR, sx = seg * kPfSegRow;
     float w[kPfSegRow + 2 * kFirHalf];
 #pragma unroll
     for (int t = 0; t < kPfSegRow + 2 * kFirHalf; ++t) w[t] = s_in[ly][sx + t];
@@ -332,11 +345,13 @@ __global__ void __launch_bounds__(kThreads) k_prefilter(DevPlan p, Src src, int 
     __syncthreads();
     const int P = p.img_pitch;
     float4* q4 = p.coef_q4 + b * p.bs_img;
-    for (int idx = tid; idx < kPfRows * kPfQuads; idx += kThreads) {
-      const int y = idx / kPfQuads, lx = idx - y * kPfQuads;
-      const int gr = orow + y, c = qcol + lx;
-      if (gr < n_rows && c < P)
-        q4[static_cast<size_t>(gr + kPad) * P + c] = make_float4(s_in[y][lx], s_in[y][lx + 1], s_in[y][lx + 2], s_in[y][lx + 3]);
+    // warp w stores rows w, w + 8, ...; lane l quads l and l + 32
+    for (int y = tid >> 5; y < kPfRows; y += kThreads / 32) {
+      const int gr = orow + y;
+      if (gr >= n_rows) break;  // rows only grow along the loop
+      float4* dst = q4 + static_cast<size_t>(gr + kPad) * P + qcol;
+      for (int lx = tid & 31; lx < kPfQuads && qcol + lx < P; lx += 32)
+        dst[lx] = make_float4(s_in[y][lx], s_in[y][lx + 1], s_in[y][lx + 2], s_in[y][lx + 3]);
     }
   }
 }
