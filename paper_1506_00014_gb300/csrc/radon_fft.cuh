@@ -488,6 +488,56 @@ struct InplaceChain {
   }
 };
 
+// One out-of-place Stockham pass (same butterflies and output order as inplace_pass): each
+// butterfly reads its inputs through `in` and writes through `out` at once, so a pass needs one
+// barrier (after its stores) instead of two, at the cost of a second buffer.
+template <int NN, int G, int TH, int R, int NS, bool INV, class In, class Out>
+__device__ __forceinline__ void pingpong_pass(const float2* __restrict__ tw, const In& in, const Out& out, int tid) {
+  constexpr int NBF = NN / R;
+  constexpr int NB = G * NBF;
+  constexpr int BM = (NB + TH - 1) / TH;
+  constexpr bool kExact = BM * TH == NB;
+#pragma unroll
+  for (int i = 0; i < BM; ++i) {
+    const int t = tid + i * TH;
+    if (!kExact && t >= NB) break;
+    const int g = t % G, j = t / G;
+    const int k = j % NS, q = j / NS;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in(j + r * NBF, g);
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tw[k * (R - 1) + r - 1];
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      }
+    }
+    Dft<R, INV>::run(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) out(q * NS * R + k + r * NS, g, v[Dft<R, INV>::idx(r)]);
+  }
+  if constexpr (Out::kShared) __syncthreads();
+}
+
+// A whole transform as a chain of out-of-place passes alternating between two buffers: the first
+// pass reads `in` and writes `a`, the next reads `a` and writes `b`, and so on; the last writes
+// through `out`.
+template <int NN, int G, int TH, bool INV, int NS, int TWO, int R, int... Rest>
+struct PingPongChain {
+  template <class In, class Out>
+  __device__ __forceinline__ static void run(const float2* __restrict__ tw, const In& in, float2* a, float2* b,
+                                             const Out& out, int tid) {
+    if constexpr (sizeof...(Rest) == 0) {
+      pingpong_pass<NN, G, TH, R, NS, INV>(tw + TWO, in, out, tid);
+    } else {
+      pingpong_pass<NN, G, TH, R, NS, INV>(tw + TWO, in, SmemOut<G>{a}, tid);
+      PingPongChain<NN, G, TH, INV, NS * R, TWO + pass_twiddles(R, NS), Rest...>::run(tw, SmemIn<G>{a}, b, a, out,
+                                                                                       tid);
+    }
+  }
+};
+
 template <int... Rs>
 __host__ __device__ constexpr int chain_length() {
   int n = 1;

@@ -939,13 +939,20 @@ struct ColumnStore {
   }
 };
 
+// The radix-7 lengths (1372, 2744) run their passes out of place between two buffers: their
+// registers already hold them to 2 CTAs per SM, so the second buffer costs no occupancy, and each
+// pass needs one barrier instead of two.
+__host__ __device__ constexpr bool column_pingpong(int nn) { return nn % 7 == 0; }
+
 template <int G, int TH, int MINB, int... Rs>
 __global__ void __launch_bounds__(TH, MINB) k_columns_fixed(DevPlan p, const float2* __restrict__ kern, int n_items) {
   constexpr int NN = chain_length<Rs...>();
   constexpr int NTW = chain_twiddles<Rs...>();
+  constexpr bool PP = column_pingpong(NN);
   extern __shared__ __align__(16) float2 smem[];
   float2* data = smem;
-  float2* tw = smem + NN * G;
+  float2* data2 = smem + NN * G;  // second buffer (PP)
+  float2* tw = smem + (PP ? 2 : 1) * NN * G;
   stage_table(tw, p.tw_col, NTW, threadIdx.x, blockDim.x);
   // (the first pass's barrier orders these stores before any twiddle read)
   const int ngroups = (p.nc + G) / G;
@@ -956,11 +963,21 @@ __global__ void __launch_bounds__(TH, MINB) k_columns_fixed(DevPlan p, const flo
     const int kr0 = gi * G;
     const ColumnLoad<G> in{p.xspec + b * p.bs_x + static_cast<size_t>(m) * p.nh * p.x_pitch, p.x_pitch, p.nh, kr0,
                            p.nc};
-    const ColumnKernelStore<G, NN> mul{data, kern, kr0, p.nc};
-    InplaceChain<NN, G, TH, false, 1, 0, Rs...>::run(tw, in, data, mul, threadIdx.x);
     const ColumnStore<G, NN> out{p.yspec + b * p.bs_ys + static_cast<size_t>(m) * nrow * p.x_pitch, p.x_pitch, p.nh,
                                  kr0, p.nc};
-    InplaceChain<NN, G, TH, true, 1, 0, Rs...>::run(tw, SmemIn<G>{data}, data, out, threadIdx.x);
+    if constexpr (PP) {
+      __syncthreads();  // the previous item's last pass has read both buffers
+      // the last forward pass reads the buffer its predecessor wrote and writes the other one
+      float2* fin = (sizeof...(Rs) % 2) ? data : data2;
+      float2* oth = (sizeof...(Rs) % 2) ? data2 : data;
+      const ColumnKernelStore<G, NN> mul{fin, kern, kr0, p.nc};
+      PingPongChain<NN, G, TH, false, 1, 0, Rs...>::run(tw, in, data, data2, mul, threadIdx.x);
+      PingPongChain<NN, G, TH, true, 1, 0, Rs...>::run(tw, SmemIn<G>{fin}, oth, fin, out, threadIdx.x);
+    } else {
+      const ColumnKernelStore<G, NN> mul{data, kern, kr0, p.nc};
+      InplaceChain<NN, G, TH, false, 1, 0, Rs...>::run(tw, in, data, mul, threadIdx.x);
+      InplaceChain<NN, G, TH, true, 1, 0, Rs...>::run(tw, SmemIn<G>{data}, data, out, threadIdx.x);
+    }
   }
 }
 
@@ -1056,6 +1073,12 @@ static_assert(kNumColumnRadices == 8, "every kColumnRadices entry has an instant
 template <int G, int TH, int MINB, int... Rs>
 size_t columns_fixed_smem() {
   constexpr int NN = chain_length<Rs...>();
+  return (static_cast<size_t>(NN) * G * (column_pingpong(NN) ? 2 : 1) + chain_twiddles<Rs...>()) * sizeof(float2);
+}
+// The transposed theta pass keeps its passes in place: one buffer.
+template <int G, int TH, int MINB, int... Rs>
+size_t columns_fixed_t_smem() {
+  constexpr int NN = chain_length<Rs...>();
   return (static_cast<size_t>(NN) * G + chain_twiddles<Rs...>()) * sizeof(float2);
 }
 
@@ -1071,7 +1094,7 @@ template <int G, int TH, int MINB, int... Rs>
 cudaError_t launch_columns_fixed_t(const DevPlan& p, const float2* kern, cudaStream_t st, int batch) {
   const int n_items = (p.nc + G) / G * p.M * batch;
   const int grid = n_items < p.col_blocks_t ? n_items : p.col_blocks_t;
-  k_columns_fixed_t<G, TH, MINB, Rs...><<<grid, TH, columns_fixed_smem<G, TH, MINB, Rs...>(), st>>>(p, kern, n_items);
+  k_columns_fixed_t<G, TH, MINB, Rs...><<<grid, TH, columns_fixed_t_smem<G, TH, MINB, Rs...>(), st>>>(p, kern, n_items);
   return cudaSuccess;
 }
 
@@ -1089,7 +1112,8 @@ cudaError_t configure_columns_fixed(DevPlan& p, int optin, int n_sm) {
   auto* fn_t = k_columns_fixed_t<G, TH, MINB, Rs...>;
   int per_sm_t = 0;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fn_t, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, fn_t, TH, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, fn_t, TH, columns_fixed_t_smem<G, TH, MINB, Rs...>());
   p.col_blocks_t = per_sm_t * n_sm;  // 0: the transpose keeps the generic theta pass
   return e;
 }
