@@ -828,16 +828,16 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
 }
 
 // Back-projection rows, persistent: one CTA per resident slot walks the rows (m, jj) of every
-// slice, staging the rho twiddles once instead of once per row; each row is sampled (theta-combined
-// when the combined detector row fits in bufB), transformed and written as k_rows_fwd<true> does.
+// slice; each row is sampled (theta-combined when the combined detector row fits in bufB),
+// transformed and written as k_rows_fwd<true> does.  The rho twiddles are read through L1, so a
+// CTA holds two row buffers and, at 48 registers, five CTAs share an SM.
 template <int SEQ>
-__global__ void __launch_bounds__(kThreads) k_rows_bp_persistent(DevPlan p, int n_rows) {
+__global__ void __launch_bounds__(kThreads, 5) k_rows_bp_persistent(DevPlan p, int n_rows) {
   extern __shared__ __align__(16) float2 smem[];
   const int nc = p.nc;
   float2* bufA = smem;
   float2* bufB = smem + nc;
-  float2* tws = smem + 2 * nc;  // rows_bp_persistent is launched only when the twiddles fit (rows_tw_smem)
-  stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
+  const float2* tws = p.tw_rho;  // read through L1: two buffers per CTA leave room for a fifth CTA per SM
   float* comb = p.sino_pitch <= 2 * nc ? reinterpret_cast<float*>(bufB) : nullptr;
   const int per_slice = p.M * p.nh;
   for (int R = blockIdx.x; R < n_rows; R += gridDim.x) {
@@ -1892,10 +1892,10 @@ void launch_rows_forward(const DevPlan& p, cudaStream_t st, int batch) {
     const int blocks = n_rows < p.rows_bp_blocks ? n_rows : p.rows_bp_blocks;
     switch (p.row_fixed) {
 #define RADON_LAUNCH_ROWS_BP(i, ...) \
-  case i: k_rows_bp_persistent<i><<<blocks, kThreads, rows_smem(p), st>>>(p, n_rows); break;
+  case i: k_rows_bp_persistent<i><<<blocks, kThreads, 2 * p.nc * sizeof(float2), st>>>(p, n_rows); break;
       RADON_ROW_SEQUENCES(RADON_LAUNCH_ROWS_BP)
 #undef RADON_LAUNCH_ROWS_BP
-      default: k_rows_bp_persistent<-1><<<blocks, kThreads, rows_smem(p), st>>>(p, n_rows); break;
+      default: k_rows_bp_persistent<-1><<<blocks, kThreads, 2 * p.nc * sizeof(float2), st>>>(p, n_rows); break;
     }
     return;
   }
@@ -2059,17 +2059,18 @@ cudaError_t configure_kernels(DevPlan& p) {
     p.rows_pipe_fwd = per_sm_fwd * n_sm;
     p.rows_pipe_inv = per_sm_inv * n_sm;
   }
-  // persistent back-projection rows: when the twiddles are staged in shared memory
+  // persistent back-projection rows: for plans whose row kernels fit the twiddles in shared memory
+  // (the persistent form itself reads them through L1)
   p.rows_bp_blocks = 0;
   if (p.rows_tw_smem) {
     int n_sm = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     switch (p.row_fixed) {
 #define RADON_CONFIGURE_ROWS_BP(i, ...) \
-  case i: e = configure_persistent(k_rows_bp_persistent<i>, optin, rows_smem(p), &per_sm); break;
+  case i: e = configure_persistent(k_rows_bp_persistent<i>, optin, 2 * p.nc * sizeof(float2), &per_sm); break;
       RADON_ROW_SEQUENCES(RADON_CONFIGURE_ROWS_BP)
 #undef RADON_CONFIGURE_ROWS_BP
-      default: e = configure_persistent(k_rows_bp_persistent<-1>, optin, rows_smem(p), &per_sm);
+      default: e = configure_persistent(k_rows_bp_persistent<-1>, optin, 2 * p.nc * sizeof(float2), &per_sm);
     }
     if (e != cudaSuccess) return e;
     p.rows_bp_blocks = per_sm * n_sm;
