@@ -755,7 +755,7 @@ def run_ours(args):
         # (fine samples x 16 taps x 4 B) against n_SM x 128 B per clock at the sampled SM clock
         fine = sample_fwd_fine_samples(info)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0  # no samples: maximum clock
         l1_peak = n_sm * 128 * mhz * 1e6 / 1e9
         l1_ach = 64 * fine / (dom_ms / 1e3) / 1e9
         l1_roofline = {"fine_samples": fine, "bytes": 64 * fine, "n_sm": n_sm, "bytes_per_clock_per_sm": 128,
