@@ -317,6 +317,36 @@ struct FixedFft {
   }
 };
 
+// The same transform with the first pass (NS = 1, no twiddles) reading its inputs through a
+// functor in(i) instead of a buffer, so a caller that would first fill the buffer element by
+// element (a pre-processing step) saves that pass and its barrier.  The first pass writes a; the
+// others ping-pong between a and b.
+template <int NN, bool INV, int TH, int R, int... Rest>
+struct FixedFftIn {
+  template <class In>
+  __device__ __forceinline__ static float2* run(const In& in, float2* a, float2* b, const float2* __restrict__ tw,
+                                                int tid) {
+    constexpr int NBF = NN / R;
+#pragma unroll
+    for (int t0 = 0; t0 < NBF; t0 += TH) {
+      const int j = t0 + tid;
+      if (NBF % TH != 0 && j >= NBF) break;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = in(j + r * NBF);
+      dft<R, INV>(v);
+      float2* d = a + j * R;
+#pragma unroll
+      for (int r = 0; r < R; ++r) d[r] = v[r];
+    }
+    __syncthreads();
+    if constexpr (sizeof...(Rest) == 0)
+      return a;
+    else
+      return FixedFft<NN, INV, TH, R, Rest...>::run(a, b, tw, tid);
+  }
+};
+
 // Copy an n-entry table into shared memory (all threads; caller synchronises).
 __device__ __forceinline__ void stage_table(float2* dst, const float2* __restrict__ src, int n, int tid, int nth) {
   for (int i = tid; i < n; i += nth) dst[i] = __ldg(src + i);

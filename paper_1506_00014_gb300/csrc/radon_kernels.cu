@@ -655,6 +655,36 @@ __device__ __forceinline__ void backproject_row_cubic(const DevPlan& p, const fl
   }
 }
 
+// Cubic interpolation in s of a theta-combined detector row comb at rho sample i: taps c0 .. c0 + 3
+// around the sample's padded bin, zero outside the row.
+struct CombSample {
+  const float* comb;
+  const int2* __restrict__ bp_e;
+  int cjx;
+  float Fc;
+  int pitch;
+  __device__ __forceinline__ float operator()(int i) const {
+    const int2 ei = bp_e[i];
+    const float F = __int_as_float(ei.y) + Fc;
+    const float fl = floorf(F);
+    const int c0 = ei.x + cjx + static_cast<int>(fl) - 1;
+    float ws[4];
+    bspline_w(F - fl, ws);
+    float acc = 0.f;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int c = c0 + d;
+      acc = fmaf(ws[d], (c >= 0 && c < pitch) ? comb[c] : 0.f, acc);
+    }
+    return acc;
+  }
+};
+// Complex input k of the row transform: real samples 2k and 2k + 1.
+struct CombSamples {
+  CombSample s;
+  __device__ __forceinline__ float2 operator()(int k) const { return make_float2(s(2 * k), s(2 * k + 1)); }
+};
+
 // Cubic back-projection row with the theta interpolation done first: the four theta tap rows and
 // their weights are the same for every rho sample of the row, so they are combined once into one
 // detector row comb[c] = sum_t w_t row_t(c) (a flipped row read at K - c) in shared memory, and each
@@ -677,21 +707,9 @@ __device__ __forceinline__ void backproject_row_cubic_comb(const DevPlan& p, con
     comb[c] = acc;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < p.N_rho; i += blockDim.x) {
-    const int2 ei = p.bp_e[i];
-    const float F = __int_as_float(ei.y) + Fc;
-    const float fl = floorf(F);
-    const int c0 = ei.x + cjx + static_cast<int>(fl) - 1;  // taps c0 .. c0 + 3
-    float ws[4];
-    bspline_w(F - fl, ws);
-    float acc = 0.f;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const int c = c0 + d;
-      acc = fmaf(ws[d], (c >= 0 && c < pitch) ? comb[c] : 0.f, acc);
-    }
-    h[i] = acc;
-  }
+  if (h == nullptr) return;  // the caller's row transform samples comb itself (CombSamples)
+  const CombSample smp{comb, p.bp_e, cjx, Fc, pitch};
+  for (int i = threadIdx.x; i < p.N_rho; i += blockDim.x) h[i] = smp(i);
 }
 
 __device__ void sample_row_backproject(const DevPlan& p, int b, int m, int jj, float* __restrict__ h,
@@ -776,6 +794,11 @@ struct RowFft;
     __device__ __forceinline__ static float2* run(float2* a, float2* b, const float2* __restrict__ tw) {    \
       return FixedFft<chain_length<__VA_ARGS__>(), INV, kThreads, 1, __VA_ARGS__>::run(a, b, tw, threadIdx.x); \
     }                                                                                                      \
+    template <class In>                                                                                    \
+    __device__ __forceinline__ static float2* run_in(const In& in, float2* a, float2* b,                   \
+                                                     const float2* __restrict__ tw) {                      \
+      return FixedFftIn<chain_length<__VA_ARGS__>(), INV, kThreads, __VA_ARGS__>::run(in, a, b, tw, threadIdx.x); \
+    }                                                                                                      \
   };                                                                                                       \
   static_assert(row_radices_match<__VA_ARGS__>(kRowRadices[i]), "row radix table");
 RADON_ROW_SEQUENCES(RADON_ROW_FFT)
@@ -789,6 +812,17 @@ __device__ __forceinline__ const float2* row_fft(float2* a, float2* b, const Dev
     return fft_block<INV>(a, b, 1, p.nc, p.rad_rho, tw, threadIdx.x, blockDim.x);
   else
     return RowFft<SEQ, INV>::run(a, b, tw);
+}
+
+// Forward complex transform whose first pass reads in(k) (compiled transforms only; SEQ < 0 is
+// never called).
+template <int SEQ, class In>
+__device__ __forceinline__ const float2* row_fft_in(const In& in, float2* a, float2* b, const DevPlan& p,
+                                                   const float2* tw) {
+  if constexpr (SEQ < 0)
+    return nullptr;
+  else
+    return RowFft<SEQ, false>::run_in(in, a, b, tw);
 }
 
 // Sample one angular row, real FFT along rho, write the half spectrum (N_rho/2 + 1 bins).
@@ -842,10 +876,19 @@ __global__ void __launch_bounds__(kThreads, 5) k_rows_bp_persistent(DevPlan p, i
   const int per_slice = p.M * p.nh;
   for (int R = blockIdx.x; R < n_rows; R += gridDim.x) {
     const int b = R / per_slice, mj = R - b * per_slice, m = mj / p.nh, jj = mj - m * p.nh;
-    __syncthreads();  // the previous row's buffers (and, the first time, the staged twiddles)
-    sample_row_backproject(p, b, m, jj, reinterpret_cast<float*>(bufA), comb);
-    __syncthreads();
-    const float2* Z = row_fft<false, SEQ>(bufA, bufB, p, tws);
+    __syncthreads();  // the previous row's buffers
+    const float2* Z;
+    if (SEQ >= 0 && comb && p.interp == 3) {
+      // the compiled transform's first pass samples the combined row (in bufB) itself
+      sample_row_backproject(p, b, m, jj, nullptr, comb);
+      const int2 cj = p.bp_c[jj];
+      Z = row_fft_in<SEQ>(CombSamples{CombSample{comb, p.bp_e, cj.x, __int_as_float(cj.y), p.sino_pitch}}, bufA,
+                          bufB, p, tws);
+    } else {
+      sample_row_backproject(p, b, m, jj, reinterpret_cast<float*>(bufA), comb);
+      __syncthreads();
+      Z = row_fft<false, SEQ>(bufA, bufB, p, tws);
+    }
     float2* out = p.xspec + b * p.bs_x + static_cast<size_t>(mj) * p.x_pitch;
     for (int k = threadIdx.x; k <= nc; k += blockDim.x) {
       const float2 zk = Z[k == nc ? 0 : k];
@@ -1167,6 +1210,21 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // to even), two staging buffers of x_pitch entries, one work buffer of nc.
 __host__ __device__ __forceinline__ int rows_pipe_stage0(const DevPlan& p) { return (p.nc + 1) & ~1; }
 
+// Input k of the inverse real transform's half-length complex FFT, from the half spectrum X
+// (k in [0, nc)): Z_k = (X_k + conj X_{nc-k}) + i (X_k - conj X_{nc-k}) exp(+2 pi i k / N_rho).
+struct C2RInput {
+  const float2* X;
+  const float2* __restrict__ tw_r2c;
+  int nc;
+  __device__ __forceinline__ float2 operator()(int k) const {
+    const float2 xk = X[k];
+    const float2 xc = cconj(X[nc - k]);
+    const float2 sm = cadd(xk, xc);
+    const float2 df = cmulc(csub(xk, xc), tw_r2c[k]);
+    return make_float2(sm.x - df.y, sm.y + df.x);
+  }
+};
+
 // Copy the first 16-byte chunks [0, chunks) of a spectrum-scratch row into shared memory.
 __device__ __forceinline__ void prefetch_row(float2* dst, const float2* __restrict__ src, int chunks) {
   for (int c = threadIdx.x; c < chunks; c += blockDim.x) cp_async16(dst + 2 * c, src + 2 * c);
@@ -1238,15 +1296,15 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv_pipe(DevPlan p, int n_row
     cp_async_commit();
     cp_async_wait_prev();
     __syncthreads();
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-      const float2 xk = X[k];
-      const float2 xc = cconj(X[nc - k]);
-      const float2 sm = cadd(xk, xc);
-      const float2 df = cmulc(csub(xk, xc), p.tw_r2c[k]);  // (X_k - conj X_{n-k}) exp(+2 pi i k / N_rho)
-      work[k] = make_float2(sm.x - df.y, sm.y + df.x);       // + i * df
+    const float2* Z;
+    if constexpr (SEQ >= 0) {
+      // the compiled transform's first pass forms its inputs from the staged row itself
+      Z = RowFft<SEQ, true>::run_in(C2RInput{X, p.tw_r2c, nc}, work, const_cast<float2*>(X), tws);
+    } else {
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) work[k] = C2RInput{X, p.tw_r2c, nc}(k);
+      __syncthreads();
+      Z = row_fft<true, SEQ>(work, const_cast<float2*>(X), p, tws);
     }
-    __syncthreads();
-    const float2* Z = row_fft<true, SEQ>(work, const_cast<float2*>(X), p, tws);
     const float* h = reinterpret_cast<const float*>(Z);
     const int b = R / per_slice, mr = R - b * per_slice;  // mr = m nrow + row
     float* y = p.ylp + b * p.bs_y + static_cast<size_t>(mr) * p.y_pitch;
