@@ -347,6 +347,74 @@ struct FixedFftIn {
   }
 };
 
+// The same pass with its outputs written through a functor out(i, value) (the last pass of a
+// transform whose result goes straight to global memory); no barrier follows it.
+template <int NN, int R, int NS, bool INV, int TH, class Out>
+__device__ __forceinline__ void stockham_pass_fixed_out(const float2* __restrict__ src, const Out& out,
+                                                        const float2* __restrict__ tw, int tid) {
+  constexpr int NBF = NN / R, TSTEP = NN / (NS * R);
+#pragma unroll
+  for (int t0 = 0; t0 < NBF; t0 += TH) {
+    const int j = t0 + tid;
+    if (NBF % TH != 0 && j >= NBF) break;
+    const int q = j / NS, k = j - q * NS;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[j + r * NBF];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tw[r * k * TSTEP];
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      }
+    }
+    dft<R, INV>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) out(q * NS * R + k + r * NS, v[r]);
+  }
+}
+
+// Passes after the first, ping-ponging between a and b, the last one writing through out.
+template <int NN, bool INV, int TH, int NS, int R, int... Rest>
+struct FixedFftOut {
+  template <class Out>
+  __device__ __forceinline__ static void run(float2* a, float2* b, const float2* __restrict__ tw, const Out& out,
+                                             int tid) {
+    if constexpr (sizeof...(Rest) == 0) {
+      stockham_pass_fixed_out<NN, R, NS, INV, TH>(a, out, tw, tid);
+    } else {
+      stockham_pass_fixed<NN, R, NS, INV, TH>(a, b, tw, tid);
+      __syncthreads();
+      FixedFftOut<NN, INV, TH, NS * R, Rest...>::run(b, a, tw, out, tid);
+    }
+  }
+};
+
+// First pass through in (writes a), last pass through out: a transform from a computed input to a
+// computed destination with no staging pass at either end.
+template <int NN, bool INV, int TH, int R, int R2, int... Rest>
+struct FixedFftInOut {
+  template <class In, class Out>
+  __device__ __forceinline__ static void run(const In& in, float2* a, float2* b, const float2* __restrict__ tw,
+                                             const Out& out, int tid) {
+    constexpr int NBF = NN / R;
+#pragma unroll
+    for (int t0 = 0; t0 < NBF; t0 += TH) {
+      const int j = t0 + tid;
+      if (NBF % TH != 0 && j >= NBF) break;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = in(j + r * NBF);
+      dft<R, INV>(v);
+      float2* d = a + j * R;
+#pragma unroll
+      for (int r = 0; r < R; ++r) d[r] = v[r];
+    }
+    __syncthreads();
+    FixedFftOut<NN, INV, TH, R, R2, Rest...>::run(a, b, tw, out, tid);
+  }
+};
+
 // Copy an n-entry table into shared memory (all threads; caller synchronises).
 __device__ __forceinline__ void stage_table(float2* dst, const float2* __restrict__ src, int n, int tid, int nth) {
   for (int i = tid; i < n; i += nth) dst[i] = __ldg(src + i);

@@ -799,6 +799,11 @@ struct RowFft;
                                                      const float2* __restrict__ tw) {                      \
       return FixedFftIn<chain_length<__VA_ARGS__>(), INV, kThreads, __VA_ARGS__>::run(in, a, b, tw, threadIdx.x); \
     }                                                                                                      \
+    template <class In, class Out>                                                                         \
+    __device__ __forceinline__ static void run_in_out(const In& in, float2* a, float2* b,                  \
+                                                      const float2* __restrict__ tw, const Out& out) {     \
+      FixedFftInOut<chain_length<__VA_ARGS__>(), INV, kThreads, __VA_ARGS__>::run(in, a, b, tw, out, threadIdx.x); \
+    }                                                                                                      \
   };                                                                                                       \
   static_assert(row_radices_match<__VA_ARGS__>(kRowRadices[i]), "row radix table");
 RADON_ROW_SEQUENCES(RADON_ROW_FFT)
@@ -1225,6 +1230,23 @@ struct C2RInput {
   }
 };
 
+// Output i of the inverse transform (real samples 2i, 2i + 1 of the row) to a log-polar row y
+// of N_rho values plus kPad periodic wrap columns on each side (y[c + kPad] = h[c mod N_rho] for
+// c in [-kPad, N_rho + kPad)).
+struct RealRowOut {
+  float* y;
+  int nr;
+  __device__ __forceinline__ void operator()(int i, float2 v) const {
+    const int s = 2 * i;
+    y[s + kPad] = v.x;
+    y[s + 1 + kPad] = v.y;
+    if (s < kPad) y[s + nr + kPad] = v.x;
+    if (s + 1 < kPad) y[s + 1 + nr + kPad] = v.y;
+    if (s >= nr - kPad) y[s - nr + kPad] = v.x;
+    if (s + 1 >= nr - kPad) y[s + 1 - nr + kPad] = v.y;
+  }
+};
+
 // Copy the first 16-byte chunks [0, chunks) of a spectrum-scratch row into shared memory.
 __device__ __forceinline__ void prefetch_row(float2* dst, const float2* __restrict__ src, int chunks) {
   for (int c = threadIdx.x; c < chunks; c += blockDim.x) cp_async16(dst + 2 * c, src + 2 * c);
@@ -1296,21 +1318,20 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv_pipe(DevPlan p, int n_row
     cp_async_commit();
     cp_async_wait_prev();
     __syncthreads();
-    const float2* Z;
+    const int b = R / per_slice, mr = R - b * per_slice;  // mr = m nrow + row
+    float* y = p.ylp + b * p.bs_y + static_cast<size_t>(mr) * p.y_pitch;
     if constexpr (SEQ >= 0) {
-      // the compiled transform's first pass forms its inputs from the staged row itself
-      Z = RowFft<SEQ, true>::run_in(C2RInput{X, p.tw_r2c, nc}, work, const_cast<float2*>(X), tws);
+      // the compiled transform's first pass forms its inputs from the staged row itself, and its
+      // last pass writes the real row (with its wrap columns) straight to the log-polar array
+      RowFft<SEQ, true>::run_in_out(C2RInput{X, p.tw_r2c, nc}, work, const_cast<float2*>(X), tws, RealRowOut{y, nr});
     } else {
       for (int k = threadIdx.x; k < nc; k += blockDim.x) work[k] = C2RInput{X, p.tw_r2c, nc}(k);
       __syncthreads();
-      Z = row_fft<true, SEQ>(work, const_cast<float2*>(X), p, tws);
-    }
-    const float* h = reinterpret_cast<const float*>(Z);
-    const int b = R / per_slice, mr = R - b * per_slice;  // mr = m nrow + row
-    float* y = p.ylp + b * p.bs_y + static_cast<size_t>(mr) * p.y_pitch;
-    for (int c = static_cast<int>(threadIdx.x) - kPad; c < nr + kPad; c += blockDim.x) {
-      const int src = c < 0 ? c + nr : (c >= nr ? c - nr : c);
-      y[c + kPad] = h[src];
+      const float* h = reinterpret_cast<const float*>(row_fft<true, SEQ>(work, const_cast<float2*>(X), p, tws));
+      for (int c = static_cast<int>(threadIdx.x) - kPad; c < nr + kPad; c += blockDim.x) {
+        const int src = c < 0 ? c + nr : (c >= nr ? c - nr : c);
+        y[c + kPad] = h[src];
+      }
     }
     __syncthreads();
   }
