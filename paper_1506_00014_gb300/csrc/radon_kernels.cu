@@ -655,6 +655,8 @@ __device__ __forceinline__ void backproject_row_cubic(const DevPlan& p, const fl
   }
 }
 
+constexpr int kCombGuard = 4;  // zero cells on each side of a theta-combined row in shared memory
+
 // Cubic interpolation in s of a theta-combined detector row comb at rho sample i: taps c0 .. c0 + 3
 // around the sample's padded bin, zero outside the row.
 struct CombSample {
@@ -667,15 +669,14 @@ struct CombSample {
     const int2 ei = bp_e[i];
     const float F = __int_as_float(ei.y) + Fc;
     const float fl = floorf(F);
-    const int c0 = ei.x + cjx + static_cast<int>(fl) - 1;
+    // taps c0 .. c0 + 3; comb has kCombGuard zero cells on each side, so a block that leaves the
+    // row reads zeros, and one wholly outside it is moved into the guard band (still zeros)
+    const int c0 = clampi(ei.x + cjx + static_cast<int>(fl) - 1, -kCombGuard, pitch);
     float ws[4];
     bspline_w(F - fl, ws);
     float acc = 0.f;
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const int c = c0 + d;
-      acc = fmaf(ws[d], (c >= 0 && c < pitch) ? comb[c] : 0.f, acc);
-    }
+    for (int d = 0; d < 4; ++d) acc = fmaf(ws[d], comb[c0 + d], acc);
     return acc;
   }
 };
@@ -696,15 +697,24 @@ __device__ __forceinline__ void backproject_row_cubic_comb(const DevPlan& p, con
                                                            float Fc, float* __restrict__ h, float* __restrict__ comb) {
   const int pitch = p.sino_pitch;
   const int K = p.n_det + 2 * kPad;  // padded index of a flipped tap: K - c
-  for (int c = threadIdx.x; c < pitch; c += blockDim.x) {
+  // columns c <= K: both c and K - c lie inside the padded row, no test needed
+  const int cin = K + 1 < pitch ? K + 1 : pitch;
+  for (int c = threadIdx.x; c < cin; c += blockDim.x) {
     float acc = 0.f;
 #pragma unroll
-    for (int dt = 0; dt < 4; ++dt) {
-      const int idx = flip[dt] ? K - c : c;  // flip[] is uniform over the CTA
-      const float x = (idx >= 0 && idx < pitch) ? __ldg(rows[dt] + idx) : 0.f;
-      acc = fmaf(wt[dt], x, acc);
-    }
+    for (int dt = 0; dt < 4; ++dt) acc = fmaf(wt[dt], __ldg(rows[dt] + (flip[dt] ? K - c : c)), acc);  // flip[] is uniform over the CTA
     comb[c] = acc;
+  }
+  // the alignment columns past K (at most 3): a flipped row has no tap there
+  for (int c = cin + static_cast<int>(threadIdx.x); c < pitch; c += blockDim.x) {
+    float acc = 0.f;
+#pragma unroll
+    for (int dt = 0; dt < 4; ++dt) acc = fmaf(wt[dt], flip[dt] ? 0.f : __ldg(rows[dt] + c), acc);
+    comb[c] = acc;
+  }
+  if (threadIdx.x < kCombGuard) {
+    comb[static_cast<int>(threadIdx.x) - kCombGuard] = 0.f;
+    comb[pitch + threadIdx.x] = 0.f;
   }
   __syncthreads();
   if (h == nullptr) return;  // the caller's row transform samples comb itself (CombSamples)
@@ -844,7 +854,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(DevPlan p) {
     if (p.rows_tw_smem) stage_table(tws, p.tw_rho, nc, threadIdx.x, blockDim.x);
     tw = p.rows_tw_smem ? tws : p.tw_rho;
     // bufB (free until the FFT) holds the theta-combined detector row when it fits
-    float* comb = p.sino_pitch <= 2 * nc ? reinterpret_cast<float*>(bufB) : nullptr;
+    float* comb = p.sino_pitch + 2 * kCombGuard <= 2 * nc ? reinterpret_cast<float*>(bufB) + kCombGuard : nullptr;
     sample_row_backproject(p, b, m, jj, reinterpret_cast<float*>(bufA), comb);
   } else {  // the row sampled by k_sample_fwd, read as nc complex values
     float2* tws = smem + 2 * nc;
@@ -877,7 +887,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_rows_bp_persistent(DevPlan p, i
   float2* bufA = smem;
   float2* bufB = smem + nc;
   const float2* tws = p.tw_rho;  // read through L1: two buffers per CTA leave room for a fifth CTA per SM
-  float* comb = p.sino_pitch <= 2 * nc ? reinterpret_cast<float*>(bufB) : nullptr;
+  float* comb = p.sino_pitch + 2 * kCombGuard <= 2 * nc ? reinterpret_cast<float*>(bufB) + kCombGuard : nullptr;
   const int per_slice = p.M * p.nh;
   for (int R = blockIdx.x; R < n_rows; R += gridDim.x) {
     const int b = R / per_slice, mj = R - b * per_slice, m = mj / p.nh, jj = mj - m * p.nh;
