@@ -135,6 +135,35 @@ def test_fbp_matches_oracle(rl, N, na, nd, interp, M):
         assert _rel(got, ref) < TOL, (name, _rel(got, ref))
 
 
+# One shape per sampling-kernel variant (r = 4, 5, 6 sub-angles and r = 7 on the one-warp-per-row
+# form) and the two radix-7 theta lengths (1372, 2744).
+INVARIANT_CASES = [
+    (120, 180, 170, 3, 3),
+    (128, 128, 192, 3, 3),
+    (100, 100, 150, 3, 4),
+    (200, 150, 310, 3, 3),
+    (64, 2048, 96, 3, 3),
+    (64, 4096, 96, 3, 3),
+]
+
+
+@pytest.mark.parametrize("N,na,nd,interp,M", INVARIANT_CASES)
+def test_scaling_by_two_is_exact_and_runs_repeat_bit_for_bit(rl, N, na, nd, interp, M):
+    """R and R# are linear and every step is a sum of products of the input with data-independent
+    weights, so scaling the input by 2 (exact in FP32) scales each output exactly; no step depends
+    on the run (no atomics in R or R#), so a repeated call gives the same bits."""
+    plan = rl.radon_plan_create(N, na, nd, interp, M)
+    f = ellipse_image(N, random_ellipses(10, 41)) + 0.3 * smooth_random_image(N, 42)
+    g = random_sinogram(na, nd, 43)
+    rf = _gpu_forward(rl, plan, f)
+    assert np.array_equal(_gpu_forward(rl, plan, 2.0 * f), 2.0 * rf)
+    assert np.array_equal(_gpu_forward(rl, plan, f), rf)
+    bg = _gpu_back(rl, plan, g)
+    assert np.array_equal(_gpu_back(rl, plan, 2.0 * g), 2.0 * bg)
+    assert np.array_equal(_gpu_back(rl, plan, g), bg)
+    assert np.count_nonzero(rf) > 0 and np.count_nonzero(bg) > 0
+
+
 def test_zero_and_out_of_support_inputs_give_exact_zeros(rl):
     N, na, nd = 64, 64, 96
     plan = rl.radon_plan_create(N, na, nd, 3, 3)
